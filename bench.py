@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""DoG blob-detection benchmark on the PLIF-shaped stream workload.
+
+Workload: 1024x1024 12-bit frames (uint16, ~2000 Gaussian blobs with
+log-normal sizes on a plume background, Poisson shot noise), 25 scales
+sigma = 0.8 * 1.1^i, truncate 4, threshold 0.05, overlap 0.5, 32 log-volume
+bins.  One step = the whole path (candidates, pruning, histogram) over a batch
+of frames resident in HBM, larger than L2 in total.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank detects its own
+frames (no collective on the data path; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoG megapixels/s & HBM-roofline fraction at 1024², 25 scales; p99 frame latency"
+UNIT = "MP/s"
+WORKLOAD = "plif_stream_1024x1024_u16_25scales"
+H = W = 1024
+MP_PER_FRAME = H * W / 1e6
+REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x100: "display_clock_setting"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=96, help="frames per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(frames):
+    return {"workload": WORKLOAD, "frame": "%dx%d" % (H, W), "input": "uint16 12-bit counts",
+            "frames_per_step": frames, "scales": 25, "sigma": "0.8*1.1^i", "truncate": 4.0,
+            "threshold": 0.05, "overlap": 0.5, "nbins": 32,
+            "l2": "inputs larger than L2 (%d MiB per step)" % (frames * H * W * 2 >> 20)}
+
+
+def make_frames(n, seed0):
+    import multiprocessing as mp
+    from paper_2010_08486_gb300 import synth
+    seeds = [seed0 + f for f in range(n)]
+    if n <= 2:
+        return [synth.plif_frame_u16(s) for s in seeds]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 4)) as pool:
+        return pool.map(synth.plif_frame_u16, seeds)
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        mhz, mx, reasons = [], 0.0, set()
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                mhz.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+                bits = int(f[4], 16)
+                for b, name in REASON_BITS.items():
+                    if bits & b and name != "gpu_idle":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fused_traffic(frames_per_launch):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    scaled to this launch by frames; None if the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2010_08486_gb300", "csrc", "dog_fused.cu"), "rb").read()
+        if rec.get("kernel_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec["dram_bytes_per_frame"] * frames_per_launch
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(frames_u16, budget_s=20.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    from paper_2010_08486_gb300 import synth
+    p = oracle.OracleParams(min_sigma=0.8, ratio=1.1, n_levels=25, threshold=0.05)
+    t0 = time.perf_counter()
+    n = 0
+    for c in frames_u16:
+        oracle.detect(synth.u16_to_f32(c).astype(np.float64), p)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n * MP_PER_FRAME / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d of the workload's 1024x1024 frames through the whole path (%.1f s)" % (n, dt)}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2010_08486_gb300 import synth
+    frames = make_frames(a.warmup + a.steps, synth.PLIF_SEED_BASE)
+    import oracle
+    p = oracle.OracleParams(min_sigma=0.8, ratio=1.1, n_levels=25, threshold=0.05)
+    for c in frames[:a.warmup]:
+        oracle.detect(synth.u16_to_f32(c).astype(np.float64), p)
+    t0 = time.perf_counter()
+    for c in frames[a.warmup:]:
+        oracle.detect(synth.u16_to_f32(c).astype(np.float64), p)
+    dt = time.perf_counter() - t0
+    value = a.steps * MP_PER_FRAME / dt
+    cores = oracle.num_threads()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000 * dt / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {**workload_config(1), "frames_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one 1024x1024 frame per step through the FP64 oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+    from paper_2010_08486_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2010_08486_gb300 import dog, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B = a.frames
+    cap = 16384
+    counts_u16 = make_frames(B, synth.PLIF_SEED_BASE + rank * B)
+    host = torch.from_numpy(np.stack([c.view(np.int16) for c in counts_u16])).pin_memory()
+    frames = host.cuda()
+    det = dog.Detector(dog.plif_config(blob_cap=cap))
+    flist = [frames[i] for i in range(B)]
+    table = det.frame_table(flist, cap)
+    out = torch.empty((B * cap, 5), dtype=torch.int32, device="cuda")
+    counts = torch.zeros(B, dtype=torch.int32, device="cuda")
+    hists = torch.zeros((B, det.nbins_out), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        det.detect_batched(None, table=table, out=out, counts=counts, hists=hists, stream=stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert det.status() == 0
+    det.profile(True)
+    det.profile_read()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(a.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    fused_ms, n_fused = det.profile_read()
+    det.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * B * a.steps * MP_PER_FRAME / (ms / 1000.0)
+    n_blobs = int(counts.sum().item())
+
+    # roofline of the dominant kernel (the fused detection kernel)
+    sig = det.sigmas
+    taps = sum(2 * r + 1 for r in det.radii)
+    flop_per_px = 2 * 2 * taps                       # two separable passes, FMA = 2 flop
+    flops_per_launch = flop_per_px * H * W * B
+    launch_s = fused_ms / max(n_fused, 1) / 1000.0
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = flops_per_launch / launch_s / 1e12
+    traffic = fused_traffic(B)
+    alg_bytes = B * H * W * 2 + n_blobs * 20
+    hbm_peak = float(peaks.get("hbm_gbs", 6780.0))
+    hbm_gbs = alg_bytes / launch_s / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(B),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "traffic": traffic,
+                         "kernel": "dog_fused_kernel (batched)", "flop_per_px": flop_per_px,
+                         "peak_source": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (
+                             props.multi_processor_count, sm_max)},
+            "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
+                    "bytes_per_px": 2, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "gpu_launches": 5 * a.steps,
+            "blobs_per_frame": n_blobs / B}
+    clk_s = clk.summary()
+    if clk_s:
+        line["clocks"] = clk_s
+
+    # end to end through the public API: pinned host frames in, histograms and counts out
+    if not a.no_e2e:
+        counts_h = torch.zeros_like(counts, device="cpu").pin_memory()
+        hists_h = torch.zeros_like(hists, device="cpu").pin_memory()
+
+        def e2e_step():
+            frames.copy_(host, non_blocking=True)
+            step()
+            counts_h.copy_(counts, non_blocking=True)
+            hists_h.copy_(hists, non_blocking=True)
+
+        for _ in range(a.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        line["e2e"] = {"value": world * B * a.steps * MP_PER_FRAME / (e_ms / 1000.0), "unit": UNIT,
+                       "h2d_bytes_per_step": int(host.numel() * host.element_size()),
+                       "d2h_bytes_per_step": int(counts.numel() * 4 + hists.numel() * 4)}
+
+    # per-frame latency: one frame at a time through dog_detect, row bands of 128
+    det.set_tiling(128)
+    lat = []
+    blobs = dog.empty_blobs(cap, "cuda")
+    hist1 = torch.zeros(det.nbins_out, dtype=torch.int32, device="cuda")
+    for i in range(min(B, 64) + 3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        det.detect(flist[i % B], out=blobs, hist=hist1, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= 3:
+            lat.append(e0.elapsed_time(e1))
+    det.set_tiling(0)
+    lat.sort()
+    line["latency_ms"] = {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                          "frames": len(lat), "mode": "single frame, dog_detect, 128-row bands"}
+
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(counts_u16)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

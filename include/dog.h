@@ -1,0 +1,247 @@
+/*
+ * dog.h - C ABI of the GB300 (sm_103a) Difference-of-Gaussians blob detector.
+ *
+ * Method: arXiv 2010.08486, "Towards Online Steering of Flame Spray Pyrolysis
+ * Nanoparticle Synthesis".  Sec. 3 defines the scale space L = g(sigma) * I;
+ * Sec. 4 the sigma ladder (Eq. 1), adjacent differences (Eq. 2), the scale
+ * normalisation (Eq. 3), the maximum-filter extremum test, pruning by overlap
+ * and the blob-volume histogram; Sec. 4.1 the 3x3x3 maximum pooling, the
+ * threshold Thresh = (MaxPool3D(D) - D == 0) and (D > 0.1), and coalescing of
+ * blobs whose normalised overlap exceeds 0.5.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named d_* are CUDA device pointers owned by the caller; h_*
+ *    are host pointers.  The library never frees caller memory.
+ *  - Images are row-major, one channel, pitch counted in ELEMENTS (>= w).
+ *    dtype DOG_DTYPE_F32: float in any range (the paper's frames are in
+ *    [0, 1]).  DOG_DTYPE_U16: 12-bit counts, converted on load to
+ *    float(v) / 4095 (one IEEE single division).
+ *  - Coordinates: x = column, y = row, integer pixel centres.  `level` is the
+ *    DoG plane index i (0 .. K-2) whose sigma is sigma_i (the smaller sigma
+ *    of the pair, Eq. 3).
+ *  - The boundary is half-sample symmetric reflection (... 1 0 | 0 1 2 ...),
+ *    folded repeatedly when a kernel radius exceeds the frame.
+ *  - `stream` is a cudaStream_t (0 = legacy default stream).  Every compute
+ *    call is asynchronous and stream-ordered; it returns DOG_OK once the work
+ *    is enqueued.  Errors found later on the device (capacity overflow, a
+ *    wait that ran out) are recorded in the handle's status word, read with
+ *    dog_get_status.
+ *  - A handle owns device workspace that its calls reuse: calls on one handle
+ *    must be ordered on one stream (or otherwise serialised).  Use one handle
+ *    per concurrent stream or host thread.
+ *  - No call throws, traps or aborts; all return a dog_status code.
+ */
+#ifndef DOG_H_
+#define DOG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef enum dog_status {
+    DOG_OK = 0,
+    DOG_ERR_INVALID = -1,     /* bad argument (null pointer, size, config)       */
+    DOG_ERR_NOMEM = -2,       /* device or host allocation failed                */
+    DOG_ERR_CUDA = -3,        /* a CUDA runtime call failed                      */
+    DOG_ERR_CAPACITY = -4,    /* a blob list overflowed (true count still given) */
+    DOG_ERR_TIMEOUT = -5,     /* a bounded device wait ran out                   */
+    DOG_ERR_UNSUPPORTED = -6  /* valid but outside what this build supports      */
+} dog_status;
+
+enum { DOG_LADDER_GEOM = 0, DOG_LADDER_ARITH = 1 };
+enum { DOG_NORM_DERIV = 0, DOG_NORM_PAPER = 1 };
+enum { DOG_PRUNE_COALESCE = 0, DOG_PRUNE_SUPPRESS = 1, DOG_PRUNE_OFF = 2 };
+enum { DOG_HIST_LOGV = 0, DOG_HIST_LADDER = 1 };
+enum { DOG_DTYPE_F32 = 0, DOG_DTYPE_U16 = 1 };
+
+/* Largest ladder and radius this build accepts. */
+#define DOG_MAX_LEVELS 32
+#define DOG_MAX_RADIUS 64
+#define DOG_MAX_NBINS 256
+
+/* ---------------------------------------------------------------- config
+ * Hyper-parameters of Sec. 4 / 4.1 (n_bin = n_levels - 1, min_sigma,
+ * max_sigma, truncate, threshold, overlap) plus the readings this library
+ * takes where the paper is silent.
+ *
+ *  n_levels   Gaussian levels K (K-1 DoG planes).  0: for GEOM, derived from
+ *             max_sigma as K = floor(ln(max/min)/ln(ratio)) + 2, so the DoG
+ *             planes span [min_sigma, max_sigma].  Required for ARITH.
+ *  sigmas     optional explicit ladder (host pointer, n_levels increasing
+ *             values); copied by dog_create.  NULL: use `ladder`.
+ *  ladder     GEOM: sigma_i = min_sigma * ratio^i.  ARITH: Eq. 1,
+ *             sigma_i = min + i (max - min) / (K - 1).
+ *  truncate   kernel radius r_i = floor(truncate * sigma_i + 0.5) (Sec. 4.1).
+ *  threshold  strict lower bound on the response D (Sec. 4.1, default 0.1).
+ *  overlap    normalised disc overlap above which blobs coalesce (0.5).
+ *  norm       DERIV: c_i = sigma_i / (sigma_{i+1} - sigma_i), the finite-
+ *             difference form of sigma * dg/dsigma (Sec. 3).  PAPER: c_i =
+ *             sigma_i (Eq. 3 literally).  D_i = c_i (L_i - L_{i+1}).
+ *  prune      COALESCE (mean sigma of the group), SUPPRESS, or OFF.
+ *  nbins      LOGV bins on log volume between the first and last DoG plane;
+ *             LADDER uses one bin per DoG plane (nbins ignored).
+ *  soft_T     temperature of the soft (sigmoid) threshold, differentiable form.
+ *  max_h/max_w  largest frame a call will pass (sizes workspace).
+ *  blob_cap   candidate capacity per frame held in the workspace.
+ */
+typedef struct dog_config {
+    int32_t n_levels;
+    const double* sigmas;
+    double min_sigma, max_sigma, ratio;
+    int32_t ladder;
+    double truncate, threshold, overlap;
+    int32_t norm, prune;
+    int32_t nbins, hist_mode;
+    double soft_T;
+    int32_t max_h, max_w;
+    int32_t blob_cap;
+} dog_config;
+
+/* One blob: centre (x, y), DoG plane, sigma (the plane's sigma, or the mean
+ * sigma of a coalesced group), response D at the centre.  20 bytes.
+ * Radius r = sqrt(2) sigma, volume V = 4/3 pi r^3 (Sec. 4). */
+typedef struct dog_blob {
+    int32_t x, y, level;
+    float sigma, response;
+} dog_blob;
+
+/* One frame of a batched call (the table lives in DEVICE memory).
+ * blob_off: first slot of this frame's blobs in the output array; each frame
+ * owns blob_cap slots (dog_config.blob_cap). */
+typedef struct dog_frame {
+    const void* ptr;
+    int32_t h, w, pitch, dtype;
+    int64_t blob_off;
+} dog_frame;
+
+typedef struct dog_handle dog_t;
+
+/* Fill *cfg with the defaults: GEOM ladder 1.0 .. 10.0 ratio 1.6, truncate
+ * 4, threshold 0.1, overlap 0.5, DERIV, COALESCE, 32 LOGV bins, soft_T 0.01,
+ * max frame 1024x1024, blob_cap 65536. */
+int dog_config_default(dog_config* cfg);
+
+/* Build a detector on the current CUDA device: computes the ladder, radii,
+ * kernels (double, rounded to float) and normalisation on the host, uploads
+ * them, and allocates the workspace.  *out receives the handle (NULL on
+ * failure).  Errors: INVALID (config), UNSUPPORTED (K > DOG_MAX_LEVELS,
+ * radius > DOG_MAX_RADIUS, or shared memory needs above the device limit),
+ * NOMEM, CUDA. */
+int dog_create(const dog_config* cfg, dog_t** out);
+
+/* Release the handle and its workspace (synchronises the device).  NULL ok. */
+void dog_destroy(dog_t* h);
+
+/* Introspection (host): K, the ladder sigma_0..K-1, radii, normalisation
+ * c_0..K-2.  Any output pointer may be NULL. */
+int dog_ladder(const dog_t* h, int32_t* K, double* h_sigmas, int32_t* h_radii, double* h_norm);
+
+/* Candidates only (Sec. 4.1 Thresh): every voxel with D > threshold that no
+ * in-range 3x3x3 neighbour exceeds.  Writes up to `cap` blobs to d_blobs (in
+ * no particular order) and the TRUE count to *d_count (may exceed cap: the
+ * status word then records DOG_ERR_CAPACITY).  One fused pass: all scales of
+ * a tile from one read of the frame; D is never stored. */
+int dog_candidates(dog_t* h, const void* d_img, int32_t dtype, int32_t img_h, int32_t img_w,
+                   int32_t pitch, dog_blob* d_blobs, int32_t cap, int32_t* d_count, void* stream);
+
+/* Overlap pruning of Sec. 4.1 on a candidate list (device): visit candidates
+ * by decreasing response (ties: level, y, x); each joins the first already
+ * accepted blob it overlaps by more than `overlap` (normalised disc overlap,
+ * r = sqrt(2) sigma of each plane) or is accepted.  COALESCE reports the mean
+ * sigma of each group (summed in visiting order; the plane sigma exactly when
+ * all members share one plane), SUPPRESS drops joiners, OFF copies.  Frame
+ * size (img_h, img_w) bounds the coordinates.  n = min(*d_count, cap_in).
+ * Output: up to cap_out blobs, count in *d_nout. */
+int dog_prune(dog_t* h, const dog_blob* d_cand, const int32_t* d_count, int32_t cap_in,
+              int32_t img_h, int32_t img_w, dog_blob* d_out, int32_t cap_out, int32_t* d_nout,
+              void* stream);
+
+/* Blob-volume histogram (Sec. 4, Sec. 4.1 "Blobs are then histogrammed").
+ * d_hist: uint32 counts (nbins, or K-1 in LADDER mode), overwritten.
+ * d_hist_vol: optional (NULL ok) double sum of V per bin, overwritten.
+ * A blob whose stored sigma equals its plane's sigma (as float) is binned by
+ * its plane alone; otherwise bin = floor(nbins (ln V - lo) / (hi - lo)),
+ * clamped, lo/hi = ln V of the first/last DoG plane sigma. */
+int dog_volume_hist(dog_t* h, const dog_blob* d_blobs, const int32_t* d_count, int32_t cap,
+                    uint32_t* d_hist, double* d_hist_vol, void* stream);
+
+/* Whole method on one frame: candidates -> prune -> histogram.  d_blobs gets
+ * the pruned blobs (up to cap), *d_count their number; d_hist / d_hist_vol as
+ * in dog_volume_hist (either may be NULL). */
+int dog_detect(dog_t* h, const void* d_img, int32_t dtype, int32_t img_h, int32_t img_w,
+               int32_t pitch, dog_blob* d_blobs, int32_t cap, int32_t* d_count, uint32_t* d_hist,
+               double* d_hist_vol, void* stream);
+
+/* Batched detection of n frames of uneven sizes (d_frames: device table).
+ * One persistent launch walks all (frame, strip, row band) tiles from a work
+ * counter; then one pruning and one histogram launch cover every frame.
+ * Frame f's pruned blobs go to d_blobs[d_frames[f].blob_off ...] (at most
+ * blob_cap), its count to d_counts[f], its histogram to
+ * d_hists[f * nbins_out ...] (nbins_out = nbins, or K-1 in LADDER mode).
+ * Tile shapes come from the handle's tuning (dog_set_tiling).  h_max_h and
+ * h_max_w bound the frame sizes of this call (host values). */
+int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t h_max_h,
+                       int32_t h_max_w, dog_blob* d_blobs, int32_t* d_counts, uint32_t* d_hists,
+                       void* stream);
+
+/* Row-band height used by detection tiles (a multiple of 8, or 0 for whole
+ * frames) and the persistent grid multiplier; set by the autotuner. */
+int dog_set_tiling(dog_t* h, int32_t band_rows, int32_t ctas_per_sm);
+
+/* Differentiable form (not in the paper; used to tune the ladder).  Soft
+ * histogram over the hard 3x3x3 local maxima of D (no threshold):
+ *   H_b += sum_v sigmoid((D_v - threshold) / soft_T) kappa_b(t(sigma_l(v)))
+ * with t the normalised log volume against the handle's own ladder ends and
+ * kappa_b a triangular weight one bin wide (t clamped to the bin centres).
+ * d_sigmas: K float sigmas (device) replacing the ladder; radii stay fixed.
+ * d_soft_hist: nbins floats, ACCUMULATED (+=) so that frames can be summed. */
+int dog_soft_hist(dog_t* h, const float* d_img, int32_t img_h, int32_t img_w, int32_t pitch,
+                  const float* d_sigmas, float* d_soft_hist, void* stream);
+
+/* Backward of dog_soft_hist for dloss/dH = d_grad_hist (nbins floats).
+ * Recomputes the blur levels (none are kept from the forward) and writes
+ * dloss/dI to d_grad_img (img_h x img_w, row-major, pitch img_w, overwritten)
+ * and ACCUMULATES dloss/dsigma into d_grad_sigmas (K floats).  The maximum
+ * mask is recomputed at the given sigmas and treated as constant. */
+int dog_backward(dog_t* h, const float* d_img, int32_t img_h, int32_t img_w, int32_t pitch,
+                 const float* d_sigmas, const float* d_grad_hist, float* d_grad_img,
+                 float* d_grad_sigmas, void* stream);
+
+/* Debug/parity: write the DoG cube D (K-1 x img_h x img_w floats, row-major
+ * planes) computed by the same fused kernel as dog_candidates. */
+int dog_debug_dog(dog_t* h, const void* d_img, int32_t dtype, int32_t img_h, int32_t img_w,
+                  int32_t pitch, float* d_dog, void* stream);
+
+/* Rolling per-stream histogram for the serving loop: adds d_hist (nbins
+ * uint32) into ring slot (*d_head % window) of d_ring (window x nbins),
+ * subtracting the slot's previous content from the running sum d_sum (nbins
+ * uint32), then advances *d_head.  All device memory, one launch. */
+int dog_ring_hist_push(const uint32_t* d_hist, int32_t nbins, uint32_t* d_ring, int32_t window,
+                       uint32_t* d_sum, int32_t* d_head, void* stream);
+
+/* Measurement.  While enabled, every launch of the fused detection kernel
+ * (candidates, batched, debug and differentiable forms) is bracketed by a pair
+ * of CUDA events recorded on the launch's own stream (up to 65536 launches
+ * between reads; later ones are not timed).  dog_profile_read waits for the
+ * recorded events, returns the summed kernel time in milliseconds and the
+ * number of timed launches, and clears them. */
+int dog_profile_enable(dog_t* h, int32_t enable);
+int dog_profile_read(dog_t* h, double* h_ms, int32_t* h_launches);
+
+/* Read and clear the handle's device status word (synchronises the stream
+ * passed to the last call).  *h_status receives DOG_OK or the first error. */
+int dog_get_status(dog_t* h, int32_t* h_status);
+
+/* Human-readable name of a status code (static string). */
+const char* dog_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DOG_H_ */

@@ -1,0 +1,181 @@
+// Internal declarations of the sm_103a DoG detector (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dog.h"
+
+namespace dogk {
+
+// ---- fused strip kernel geometry --------------------------------------------
+// A CTA owns a strip of TX output columns and walks down a band of rows in
+// blocks of MB rows.  Eight warps each own a fixed set of scale levels.
+constexpr int TX = 32;
+constexpr int MB = 8;
+constexpr int NWARPS = 8;
+constexpr int NTHREADS = NWARPS * 32;
+constexpr int RING_STRIDE = 36;    // floats per row of a level's horizontal-pass ring
+constexpr int DSLOTS = MB + 2;     // rows of the DoG buffer (block + 2 rows of history)
+constexpr int RT_MAX = 48;         // radii with fully unrolled passes; larger use a loop
+constexpr int MAX_LEVELS = DOG_MAX_LEVELS;
+
+enum FusedMode : int {
+    MODE_CANDIDATES = 0,  // thresholded maxima -> blob list (+ pending strip-edge list)
+    MODE_DUMP = 1,        // write D for every voxel
+    MODE_SOFT = 2,        // soft histogram over all local maxima
+    MODE_BWD = 3,         // backward prologue: dloss/dL planes and sigma partials
+};
+
+struct LevelInfo {
+    int r;          // kernel radius
+    int e;          // chunks of MB rows the ring runs ahead: ceil(2r / MB)
+    int delta;      // MB*e - r: input-row lead of this level's horizontal pass
+    int ring_off;   // float offset of the ring in dynamic shared memory
+    int ring_rows;  // MB * (e + 1)
+    int woff;       // offset of this level's half kernel w[0..r] in the weight array
+};
+
+// Candidate found at a strip edge whose 3x3x3 neighbourhood crosses into the
+// neighbouring strip; settled by the resolve kernel.
+struct Pending {
+    int32_t frame, x, y, level;
+    float response;
+};
+
+// Work unit of the persistent batched kernel.
+struct FrameDesc {
+    const void* img;
+    int32_t h, w, pitch, dtype;
+    int64_t blob_off;
+    int32_t n_strips, n_bands;
+    int64_t tile_begin;   // prefix sum of n_strips * n_bands over earlier frames
+};
+
+struct FusedParams {
+    // single-frame mode (batched mode reads FrameDesc instead)
+    const void* img;
+    int dtype, H, W, pitch;
+    int band;              // output rows per CTA (multiple of MB)
+    int n_strips, n_bands;
+    // batched mode
+    const FrameDesc* frames;
+    int n_frames;
+    long long n_tiles;
+    const long long* ntiles_dev;  // batched: tile total written by the prep kernel
+    int* tile_counter;     // persistent work counter (reset by the last CTA)
+    int* done_counter;
+    // ladder
+    int K, P, R;
+    const float* w;        // packed half kernels
+    const float* c;        // P normalisation coefficients
+    float thr;
+    int mode;
+    // outputs
+    dog_blob* blobs;
+    int cap;
+    int* count;            // single frame: one counter; batched: per frame
+    Pending* pend;
+    int pend_cap;
+    int* pend_count;
+    float* dump;
+    // soft / backward
+    const float* kappa;    // P x nbins triangular weights per plane
+    const float* dkappa;   // P x nbins derivative wrt t
+    const float* gH;       // nbins dloss/dH
+    int nbins;
+    float inv_T;
+    float* soft_out;       // nbins (global, float accumulation)
+    float* A;              // K x H x W dloss/dL planes (MODE_BWD)
+    double* dc_acc;        // P: dloss/dc
+    double* dt_acc;        // P: dloss/dt
+    int* status;
+    // shared-memory layout (floats)
+    int in_off, in_rows, in_stride;
+    int d_off;
+    int w_off, w_total;
+    int dmin, dmax;
+    int smem_bytes;
+    int warp_nlev[NWARPS];
+    unsigned char warp_lev[NWARPS][MAX_LEVELS];
+    LevelInfo lv[MAX_LEVELS];
+};
+
+struct ResolveParams {
+    const Pending* pend;
+    const int* pend_count;
+    int pend_cap;
+    const FrameDesc* frames;  // batched: per-frame image; single: frames == nullptr
+    const void* img;
+    int dtype, H, W, pitch;
+    int K, P;
+    const float* w;
+    const float* c;
+    int woff[MAX_LEVELS];
+    int r[MAX_LEVELS];
+    int mode;
+    dog_blob* blobs;
+    int cap;
+    int* count;
+    // soft / backward
+    const float* kappa;
+    const float* dkappa;
+    const float* gH;
+    int nbins;
+    float thr, inv_T;
+    float* soft_out;
+    float* A;
+    double* dc_acc;
+    double* dt_acc;
+    int* status;
+};
+
+// ---- launchers (defined in the .cu files) -----------------------------------
+cudaError_t launch_fused(const FusedParams& p, int grid, cudaStream_t s);
+cudaError_t launch_resolve(const ResolveParams& p, int max_pending, cudaStream_t s);
+cudaError_t launch_batch_prep(const dog_frame* frames, int n, int band, int blob_cap, FrameDesc* desc,
+                              long long* cand_off, long long* out_off, int* hw, long long* ntiles,
+                              cudaStream_t s);
+
+struct PruneParams {
+    const dog_blob* cand;
+    const int* cand_count;   // per frame
+    int cap_in;
+    const long long* cand_off;  // per-frame offset of candidates (nullptr: 0)
+    int n_frames;
+    const int* frame_hw;     // 2 ints per frame (h, w) or nullptr (use H, W)
+    int H, W;
+    int P;
+    const double* sig;       // P plane sigmas (double)
+    const int* d2thr;        // P x P: squared distance below which two planes' discs conflict
+    int cell;                // grid cell edge (pixels)
+    int mode;
+    int* state;              // scratch: per candidate
+    int* target;             // scratch: per candidate
+    int* order;              // scratch: per candidate
+    dog_blob* out;
+    int cap_out;
+    const long long* out_off;  // per frame output offset (nullptr: 0)
+    int* out_count;          // per frame
+    int* status;
+    int max_rounds;
+};
+cudaError_t launch_prune(const PruneParams& p, cudaStream_t s);
+
+struct HistParams {
+    const dog_blob* blobs;
+    const int* count;        // per frame
+    int cap;
+    const long long* off;    // per frame offset (nullptr: 0)
+    int n_frames;
+    int P, nbins, mode;      // mode: DOG_HIST_LOGV / DOG_HIST_LADDER
+    const float* sig_f;      // P plane sigmas rounded to float (on-ladder test)
+    const int* level_bin;    // P: bin of an on-ladder blob
+    const double* log_sig;   // P: ln sigma of each plane (double)
+    double log_lo, log_hi;   // ln sigma of the first / last DoG plane
+    unsigned* hist;          // n_frames x nbins_out
+    double* vol;             // n_frames x nbins_out or nullptr
+};
+cudaError_t launch_hist(const HistParams& p, cudaStream_t s);
+
+}  // namespace dogk

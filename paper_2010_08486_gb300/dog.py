@@ -1,0 +1,311 @@
+"""Python API of the GB300 DoG blob detector.
+
+Every computation runs in libdog.so's CUDA kernels; this module only
+allocates device tensors with PyTorch, passes pointers and sizes through the
+C ABI (include/dog.h), and wraps results.  Method: arXiv 2010.08486, Sec. 3-4.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Sequence
+
+import torch
+
+from . import _lib
+from ._lib import check
+
+
+@dataclasses.dataclass
+class DetectorConfig:
+    """Hyper-parameters of Sec. 4 / 4.1 (see dog_config in include/dog.h)."""
+    min_sigma: float = 1.0
+    max_sigma: float = 10.0
+    ratio: float = 1.6
+    n_levels: int = 0
+    ladder: int = _lib.LADDER_GEOM
+    sigmas: Sequence[float] | None = None
+    truncate: float = 4.0
+    threshold: float = 0.1
+    overlap: float = 0.5
+    norm: int = _lib.NORM_DERIV
+    prune: int = _lib.PRUNE_COALESCE
+    nbins: int = 32
+    hist_mode: int = _lib.HIST_LOGV
+    soft_T: float = 0.01
+    max_h: int = 1024
+    max_w: int = 1024
+    blob_cap: int = 65536
+
+    def to_c(self):
+        c = _lib.DogConfig()
+        _lib.load().dog_config_default(ctypes.byref(c))
+        keep = None
+        for f in dataclasses.fields(self):
+            if f.name == "sigmas":
+                continue
+            setattr(c, f.name, getattr(self, f.name))
+        if self.sigmas is not None:
+            keep = (ctypes.c_double * len(self.sigmas))(*[float(s) for s in self.sigmas])
+            c.sigmas = ctypes.cast(keep, ctypes.POINTER(ctypes.c_double))
+            c.n_levels = len(self.sigmas)
+        return c, keep
+
+
+def small_frame_config(**kw) -> DetectorConfig:
+    """256x256 workload: ladder 1.6^i from 1 to 10, threshold 0.1."""
+    return DetectorConfig(**{**dict(min_sigma=1.0, max_sigma=10.0, ratio=1.6, threshold=0.1,
+                                    max_h=256, max_w=256, blob_cap=65536), **kw})
+
+
+def plif_config(**kw) -> DetectorConfig:
+    """PLIF-shaped 1024x1024 workload: 25 levels 0.8 * 1.1^i, threshold 0.05."""
+    return DetectorConfig(**{**dict(min_sigma=0.8, ratio=1.1, n_levels=25, threshold=0.05,
+                                    max_h=1024, max_w=1024, blob_cap=65536), **kw})
+
+
+def grad_config(**kw) -> DetectorConfig:
+    """Differentiable workload: 12 sigmas 1.25^k, threshold 0.05, T = 0.01."""
+    return DetectorConfig(**{**dict(min_sigma=1.0, ratio=1.25, n_levels=12, threshold=0.05,
+                                    soft_T=0.01, max_h=1024, max_w=1024, blob_cap=65536), **kw})
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _img_dtype(img: torch.Tensor) -> int:
+    if img.dtype == torch.float32:
+        return _lib.DTYPE_F32
+    if img.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)):
+        return _lib.DTYPE_U16
+    raise TypeError("frames must be float32 or 16-bit counts, got %s" % img.dtype)
+
+
+def _check_img(img: torch.Tensor):
+    if not img.is_cuda:
+        raise ValueError("frame must be a CUDA tensor")
+    if img.dim() != 2 or img.stride(1) != 1:
+        raise ValueError("frame must be 2-D with unit column stride")
+    return img.shape[0], img.shape[1], img.stride(0)
+
+
+@dataclasses.dataclass
+class BlobList:
+    """Device blob records: x, y, level (int32), sigma, response (float32)."""
+    raw: torch.Tensor      # (cap, 5) int32
+    count: torch.Tensor    # () int32 on the device
+
+    def n(self) -> int:
+        return int(self.count.item())
+
+    def to_numpy(self):
+        n = min(self.n(), self.raw.shape[0])
+        r = self.raw[:n].cpu()
+        ints = r[:, :3].numpy()
+        flt = r[:, 3:].view(torch.float32).numpy()
+        return ints[:, 0], ints[:, 1], ints[:, 2], flt[:, 0], flt[:, 1]
+
+
+def empty_blobs(cap: int, device) -> BlobList:
+    return BlobList(torch.empty((cap, 5), dtype=torch.int32, device=device),
+                    torch.zeros((), dtype=torch.int32, device=device))
+
+
+class Detector:
+    """One handle of the C library on the current CUDA device."""
+
+    def __init__(self, cfg: DetectorConfig | None = None, device=None):
+        self.cfg = cfg or DetectorConfig()
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        c, self._keep = self.cfg.to_c()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.dog_create(ctypes.byref(c), ctypes.byref(h)), "dog_create")
+        self.h = h
+        K = ctypes.c_int32()
+        check(self.lib.dog_ladder(self.h, ctypes.byref(K), None, None, None), "dog_ladder")
+        self.K = K.value
+        self.P = self.K - 1
+        sig = (ctypes.c_double * self.K)()
+        rad = (ctypes.c_int32 * self.K)()
+        nrm = (ctypes.c_double * self.P)()
+        check(self.lib.dog_ladder(self.h, None, sig, rad, nrm), "dog_ladder")
+        self.sigmas = list(sig)
+        self.radii = list(rad)
+        self.norm = list(nrm)
+        self.nbins_out = self.P if self.cfg.hist_mode == _lib.HIST_LADDER else self.cfg.nbins
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dog_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- forward
+    def candidates(self, img: torch.Tensor, cap: int | None = None, out: BlobList | None = None,
+                   stream=None) -> BlobList:
+        H, W, pitch = _check_img(img)
+        cap = cap or self.cfg.blob_cap
+        out = out or empty_blobs(cap, img.device)
+        check(self.lib.dog_candidates(self.h, img.data_ptr(), _img_dtype(img), H, W, pitch,
+                                      out.raw.data_ptr(), out.raw.shape[0], out.count.data_ptr(),
+                                      _stream(stream)), "dog_candidates")
+        return out
+
+    def prune(self, cand: BlobList, H: int, W: int, cap: int | None = None, stream=None) -> BlobList:
+        cap = cap or cand.raw.shape[0]
+        out = empty_blobs(cap, cand.raw.device)
+        check(self.lib.dog_prune(self.h, cand.raw.data_ptr(), cand.count.data_ptr(), cand.raw.shape[0],
+                                 H, W, out.raw.data_ptr(), cap, out.count.data_ptr(), _stream(stream)),
+              "dog_prune")
+        return out
+
+    def volume_hist(self, blobs: BlobList, with_volume: bool = False, stream=None):
+        hist = torch.zeros(self.nbins_out, dtype=torch.int32, device=blobs.raw.device)
+        vol = torch.zeros(self.nbins_out, dtype=torch.float64, device=blobs.raw.device) if with_volume else None
+        check(self.lib.dog_volume_hist(self.h, blobs.raw.data_ptr(), blobs.count.data_ptr(),
+                                       blobs.raw.shape[0], hist.data_ptr(), _ptr(vol), _stream(stream)),
+              "dog_volume_hist")
+        return hist, vol
+
+    def detect(self, img: torch.Tensor, cap: int | None = None, with_volume: bool = False,
+               out: BlobList | None = None, hist: torch.Tensor | None = None, stream=None):
+        H, W, pitch = _check_img(img)
+        cap = cap or self.cfg.blob_cap
+        out = out or empty_blobs(cap, img.device)
+        if hist is None:
+            hist = torch.zeros(self.nbins_out, dtype=torch.int32, device=img.device)
+        vol = torch.zeros(self.nbins_out, dtype=torch.float64, device=img.device) if with_volume else None
+        check(self.lib.dog_detect(self.h, img.data_ptr(), _img_dtype(img), H, W, pitch,
+                                  out.raw.data_ptr(), out.raw.shape[0], out.count.data_ptr(),
+                                  hist.data_ptr(), _ptr(vol), _stream(stream)), "dog_detect")
+        return out, hist, vol
+
+    def debug_dog(self, img: torch.Tensor, stream=None) -> torch.Tensor:
+        H, W, pitch = _check_img(img)
+        D = torch.empty((self.P, H, W), dtype=torch.float32, device=img.device)
+        check(self.lib.dog_debug_dog(self.h, img.data_ptr(), _img_dtype(img), H, W, pitch, D.data_ptr(),
+                                     _stream(stream)), "dog_debug_dog")
+        return D
+
+    def set_tiling(self, band_rows: int, ctas_per_sm: int = 1):
+        check(self.lib.dog_set_tiling(self.h, band_rows, ctas_per_sm), "dog_set_tiling")
+
+    def profile(self, enable: bool = True):
+        check(self.lib.dog_profile_enable(self.h, int(enable)), "dog_profile_enable")
+
+    def profile_read(self):
+        """(summed fused-kernel milliseconds, launches) since the last read."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int32()
+        check(self.lib.dog_profile_read(self.h, ctypes.byref(ms), ctypes.byref(n)), "dog_profile_read")
+        return ms.value, n.value
+
+    def status(self) -> int:
+        v = ctypes.c_int32()
+        check(self.lib.dog_get_status(self.h, ctypes.byref(v)), "dog_get_status")
+        return v.value
+
+    # ---------------------------------------------------------------- batched
+    def frame_table(self, frames: Sequence[torch.Tensor], blob_cap: int | None = None):
+        """Device dog_frame table for `frames`; blob slots of blob_cap per frame."""
+        cap = blob_cap or self.cfg.blob_cap
+        n = len(frames)
+        tab = (_lib.DogFrame * n)()
+        mh = mw = 0
+        for f, img in enumerate(frames):
+            H, W, pitch = _check_img(img)
+            tab[f].ptr = img.data_ptr()
+            tab[f].h, tab[f].w, tab[f].pitch = H, W, pitch
+            tab[f].dtype = _img_dtype(img)
+            tab[f].blob_off = f * cap
+            mh, mw = max(mh, H), max(mw, W)
+        host = torch.frombuffer(bytearray(bytes(tab)), dtype=torch.uint8)
+        return host.to(frames[0].device), n, mh, mw
+
+    def detect_batched(self, frames: Sequence[torch.Tensor], table=None, out: torch.Tensor | None = None,
+                       counts: torch.Tensor | None = None, hists: torch.Tensor | None = None, stream=None):
+        """Detect all frames in one persistent launch (+ one prune and one histogram launch).
+        Returns (blobs (n*cap, 5) int32, counts (n,), hists (n, nbins))."""
+        cap = self.cfg.blob_cap
+        tab, n, mh, mw = table if table is not None else self.frame_table(frames, cap)
+        dev = tab.device
+        out = out if out is not None else torch.empty((n * cap, 5), dtype=torch.int32, device=dev)
+        counts = counts if counts is not None else torch.zeros(n, dtype=torch.int32, device=dev)
+        hists = hists if hists is not None else torch.zeros((n, self.nbins_out), dtype=torch.int32, device=dev)
+        check(self.lib.dog_detect_batched(self.h, tab.data_ptr(), n, mh, mw, out.data_ptr(), counts.data_ptr(),
+                                          hists.data_ptr(), _stream(stream)), "dog_detect_batched")
+        return out, counts, hists
+
+    # --------------------------------------------------------- differentiable
+    def soft_hist(self, img: torch.Tensor, sigmas: torch.Tensor, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+        H, W, pitch = _check_img(img)
+        if out is None:
+            out = torch.zeros(self.cfg.nbins, dtype=torch.float32, device=img.device)
+        check(self.lib.dog_soft_hist(self.h, img.data_ptr(), H, W, pitch, sigmas.data_ptr(), out.data_ptr(),
+                                     _stream(stream)), "dog_soft_hist")
+        return out
+
+    def backward(self, img: torch.Tensor, sigmas: torch.Tensor, grad_hist: torch.Tensor,
+                 grad_sigmas: torch.Tensor | None = None, stream=None):
+        H, W, pitch = _check_img(img)
+        gi = torch.empty((H, W), dtype=torch.float32, device=img.device)
+        gs = grad_sigmas if grad_sigmas is not None else torch.zeros(self.K, dtype=torch.float32,
+                                                                   device=img.device)
+        check(self.lib.dog_backward(self.h, img.data_ptr(), H, W, pitch, sigmas.data_ptr(),
+                                    grad_hist.contiguous().data_ptr(), gi.data_ptr(), gs.data_ptr(),
+                                    _stream(stream)), "dog_backward")
+        return gi, gs
+
+
+def blobs_from_raw(raw: torch.Tensor, count: int):
+    r = raw[:count].cpu()
+    ints = r[:, :3].numpy()
+    flt = r[:, 3:].view(torch.float32).numpy()
+    return ints[:, 0], ints[:, 1], ints[:, 2], flt[:, 0], flt[:, 1]
+
+
+class DoGSoftHist(torch.autograd.Function):
+    """Soft blob-volume histogram of a batch of frames with learnable sigmas.
+
+    forward(frames (B, H, W) float32 CUDA, sigmas (K,) float32 CUDA, det) ->
+    H (nbins,) summed over the batch.  backward recomputes the blur levels in
+    the CUDA kernels (nothing is saved but the inputs)."""
+
+    @staticmethod
+    def forward(ctx, frames: torch.Tensor, sigmas: torch.Tensor, det: Detector):
+        frames = frames.contiguous()
+        sig = sigmas.detach().contiguous()
+        out = torch.zeros(det.cfg.nbins, dtype=torch.float32, device=frames.device)
+        for b in range(frames.shape[0]):
+            det.soft_hist(frames[b], sig, out=out)
+        ctx.save_for_backward(frames, sig)
+        ctx.det = det
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out: torch.Tensor):
+        frames, sig = ctx.saved_tensors
+        det = ctx.det
+        gs = torch.zeros(det.K, dtype=torch.float32, device=frames.device)
+        gimg = torch.empty_like(frames)
+        g = grad_out.contiguous().float()
+        for b in range(frames.shape[0]):
+            gi, _ = det.backward(frames[b], sig, g, grad_sigmas=gs)
+            gimg[b].copy_(gi)
+        return gimg, gs, None
