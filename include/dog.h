@@ -224,6 +224,15 @@ int dog_debug_dog(dog_t* h, const void* d_img, int32_t dtype, int32_t img_h, int
 int dog_ring_hist_push(const uint32_t* d_hist, int32_t nbins, uint32_t* d_ring, int32_t window,
                        uint32_t* d_sum, int32_t* d_head, void* stream);
 
+/* The same for a batch of n frames from several streams in one launch:
+ * frame f's histogram d_hists[f * nbins ...] goes to stream d_stream_ids[f]
+ * (0 <= id < n_streams), whose ring is d_rings[id * window * nbins ...], sum
+ * d_sums[id * nbins ...] and head d_heads[id].  Frames of one stream are
+ * pushed in batch order. */
+int dog_ring_hist_push_batched(const uint32_t* d_hists, const int32_t* d_stream_ids, int32_t n,
+                               int32_t nbins, int32_t n_streams, uint32_t* d_rings, int32_t window,
+                               uint32_t* d_sums, int32_t* d_heads, void* stream);
+
 /* Measurement.  While enabled, every launch of the fused detection kernel
  * (candidates, batched, debug and differentiable forms) is bracketed by a pair
  * of CUDA events recorded on the launch's own stream (up to 65536 launches

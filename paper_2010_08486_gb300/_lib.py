@@ -31,7 +31,8 @@ MAX_RADIUS = 64
 EXPORTS = (
     "dog_config_default", "dog_create", "dog_destroy", "dog_ladder", "dog_candidates", "dog_prune",
     "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_soft_hist",
-    "dog_backward", "dog_debug_dog", "dog_ring_hist_push", "dog_profile_enable", "dog_profile_read",
+    "dog_backward", "dog_debug_dog", "dog_ring_hist_push", "dog_ring_hist_push_batched",
+    "dog_profile_enable", "dog_profile_read",
     "dog_get_status", "dog_status_string",
 )
 
@@ -119,6 +120,7 @@ def load(path: str | None = None):
         lib.dog_backward.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
         lib.dog_debug_dog.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp]
         lib.dog_ring_hist_push.argtypes = [vp, i32, vp, i32, vp, vp, vp]
+        lib.dog_ring_hist_push_batched.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp, vp]
         lib.dog_profile_enable.argtypes = [vp, i32]
         lib.dog_profile_read.argtypes = [vp, P(ctypes.c_double), P(i32)]
         lib.dog_get_status.argtypes = [vp, P(i32)]

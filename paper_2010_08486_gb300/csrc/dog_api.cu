@@ -14,6 +14,8 @@
 namespace dogk {
 cudaError_t launch_ring_push(const uint32_t* hist, int nbins, uint32_t* ring, int window, uint32_t* sum,
                              int32_t* head, cudaStream_t s);
+cudaError_t launch_ring_push_batched(const uint32_t* hists, const int32_t* ids, int n, int nbins, int n_streams,
+                                     uint32_t* rings, int window, uint32_t* sums, int32_t* heads, cudaStream_t s);
 // differentiable form (dog_soft.cu)
 int soft_forward(dog_handle* h, const float* img, int H, int W, int pitch, const float* sig, float* out,
                  cudaStream_t s);
@@ -198,7 +200,8 @@ static void assign_levels(dog_handle* h) {
         int best = 0;
         for (int w = 1; w < NWARPS; ++w)
             if (load[w] < load[best]) best = w;
-        load[best] += 2 * (2 * h->rad[i] + 1) + 6;
+        // two passes of tpad/8 blocks (~80 issue slots each) plus per-level set-up
+        load[best] += 2 * (h->base.lv[i].tpad / 8) * 80 + 60;
         h->base.warp_lev[best][h->base.warp_nlev[best]++] = (unsigned char)i;
     }
 }
@@ -280,10 +283,12 @@ int dog_create(const dog_config* cfg, dog_t** out) {
         h->rad.push_back(r);
         h->R = std::max(h->R, r);
     }
-    // ---- kernels (double, rounded to float), half kernels w[0..r]
+    // ---- kernels (double, rounded to float): full taps t = 0..2r (tap t weighs
+    // the sample at offset t - r), zero-padded to a multiple of 8 taps
     std::vector<float> wf;
     for (int i = 0; i < h->K; ++i) {
         const int r = h->rad[i];
+        const int tpad = 8 * ((2 * r + 1 + 7) / 8);
         std::vector<double> e(2 * r + 1);
         double z = 0.0;
         for (int j = -r; j <= r; ++j) {
@@ -291,9 +296,8 @@ int dog_create(const dog_config* cfg, dog_t** out) {
             z += e[j + r];
         }
         h->woff.push_back((int)wf.size());
-        for (int j = 0; j <= r; ++j) wf.push_back((float)(e[j + r] / z));
+        for (int t = 0; t < tpad; ++t) wf.push_back(t <= 2 * r ? (float)(e[t] / z) : 0.0f);
     }
-    while (wf.size() % 4) wf.push_back(0.0f);
     h->w_total = (int)wf.size();
     // ---- normalisation (Eq. 3 / heat-equation finite difference)
     for (int i = 0; i < h->P; ++i)
@@ -313,13 +317,16 @@ int dog_create(const dog_config* cfg, dog_t** out) {
     b.w_off = off;
     b.w_total = h->w_total;
     off += h->w_total;
-    b.in_stride = ((TX + 2 * h->R + 31) / 32) * 32 + 1;
+    // input rows hold TX + 2R loaded columns; the padded taps of the widest
+    // level read 8 further (zero) columns; stride = 1 mod 32 for the banks
+    b.in_stride = ((TX + 2 * h->R + 8 + 31) / 32) * 32 + 1;
     for (int i = 0; i < h->K; ++i) {
         LevelInfo& L = b.lv[i];
         L.r = h->rad[i];
-        L.e = (2 * L.r + MB - 1) / MB;
+        L.tpad = 8 * ((2 * L.r + 1 + 7) / 8);
+        L.e = L.tpad / MB;
         L.delta = MB * L.e - L.r;
-        L.ring_rows = MB * (L.e + 1);
+        L.ring_rows = L.tpad + MB;
         L.woff = h->woff[i];
         dmin = std::min(dmin, L.delta);
         dmax = std::max(dmax, L.delta);
@@ -759,6 +766,17 @@ int dog_ring_hist_push(const uint32_t* d_hist, int32_t nbins, uint32_t* d_ring, 
                        uint32_t* d_sum, int32_t* d_head, void* stream) {
     if (!d_hist || !d_ring || !d_sum || !d_head || nbins < 1 || window < 1) return DOG_ERR_INVALID;
     return status_from(launch_ring_push(d_hist, nbins, d_ring, window, d_sum, d_head, (cudaStream_t)stream));
+}
+
+int dog_ring_hist_push_batched(const uint32_t* d_hists, const int32_t* d_stream_ids, int32_t n, int32_t nbins,
+                               int32_t n_streams, uint32_t* d_rings, int32_t window, uint32_t* d_sums,
+                               int32_t* d_heads, void* stream) {
+    if (!d_hists || !d_stream_ids || !d_rings || !d_sums || !d_heads || n < 0 || nbins < 1 || n_streams < 1 ||
+        window < 1)
+        return DOG_ERR_INVALID;
+    if (n == 0) return DOG_OK;
+    return status_from(launch_ring_push_batched(d_hists, d_stream_ids, n, nbins, n_streams, d_rings, window,
+                                                d_sums, d_heads, (cudaStream_t)stream));
 }
 
 int dog_profile_enable(dog_t* h, int32_t enable) {

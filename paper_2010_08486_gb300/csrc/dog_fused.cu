@@ -10,17 +10,20 @@
 // recomputed.  Each of the eight warps owns a fixed set of levels, chosen on
 // the host to balance taps.  For each block and owned level a warp
 //   1. runs the horizontal pass of the next 8 input rows into the level's
-//      shared-memory ring (which runs ceil(2r/8) blocks ahead),
-//   2. runs the vertical pass over the ring into the block's L rows,
-//   3. shifts the ring up by 8 rows.
-// Both passes are register-blocked 1-D correlations (8 outputs per lane,
-// taps unrolled for radii <= RT_MAX), summing taps in ascending order with
-// FMA from zero -- the resolve kernel below repeats the same order and so
-// reproduces any value bit for bit.  Then all threads form D in place and
-// test the previous block's rows against their 26 neighbours; survivors are
-// compacted with one warp ballot and one atomic per warp.  Neighbours in the
-// adjacent strip are not held here: a candidate at a strip edge is queued and
-// the resolve kernel recomputes the few D values it needs.
+//      circular shared-memory ring (which runs Tpad/8 blocks ahead),
+//   2. runs the vertical pass over the ring into the block's L rows.
+// Both passes are register-blocked 1-D correlations: 8 outputs per lane,
+// taps in blocks of 8 against a two-window register file whose halves swap
+// roles each block, so one short loop serves every radius and the whole
+// kernel stays resident in the instruction cache.  Kernels are zero-padded to
+// Tpad = 8 ceil((2r+1)/8) taps; taps are summed in ascending order with FMA
+// from zero, so the padding never changes a value and the resolve kernel
+// below, which repeats the order on the real taps only, reproduces any
+// response bit for bit.  Then all threads form D in place and test the
+// previous block's rows against their 26 neighbours; survivors are compacted
+// with one warp ballot and one atomic per warp.  Neighbours in the adjacent
+// strip are not held here: a candidate at a strip edge is queued and the
+// resolve kernel recomputes the few responses it needs.
 #include <cuda_runtime.h>
 
 #include "dog_internal.cuh"
@@ -28,6 +31,7 @@
 namespace dogk {
 
 __device__ __forceinline__ int refl(int i, int n) {
+    if (i >= 0 && i < n) return i;
     int p = 2 * n;
     int m = i % p;
     if (m < 0) m += p;
@@ -47,124 +51,69 @@ __device__ __forceinline__ float dog_value(float c, float a, float b) {
 }
 
 // ---------------------------------------------------------------------------
-// 1-D passes.  out[k] = sum_{t=0}^{2r} w[|t-r|] * in[k+t], k = 0..7, in
-// ascending t, starting from 0.
-template <int R>
-__device__ __forceinline__ void hpass_t(const float* __restrict__ src, float* __restrict__ dst,
-                                        const float* __restrict__ wsm) {
-    float w[R + 1];
+// 1-D passes.  out[k] = sum_{t=0}^{Tpad-1} wfull[t] * in[k+t], k = 0..7, in
+// ascending t from 0.  A holds inputs [8j, 8j+8), B inputs [8j+8, 8j+16) of
+// tap block j; the 64 products of the block are accumulated tap-major.
+__device__ __forceinline__ void fma_block(float (&acc)[8], const float (&A)[8], const float (&B)[8],
+                                          const float4 wa, const float4 wb) {
+    const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
-    for (int j = 0; j <= R; ++j) w[j] = wsm[j];
-    float acc[8];
+    for (int u = 0; u < 8; ++u)
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
+        for (int k = 0; k < 8; ++k) acc[k] = __fmaf_rn(w[u], (k + u < 8) ? A[k + u] : B[k + u - 8], acc[k]);
+}
+
+// Horizontal: inputs are consecutive floats of one shared-memory row.
+__device__ __forceinline__ void hpass(const float* __restrict__ src, float* __restrict__ dst,
+                                      const float4* __restrict__ w4, int nb) {
+    float acc[8], A[8], B[8];
 #pragma unroll
-    for (int t = 0; t < 8 + 2 * R; ++t) {
-        const float v = src[t];
+    for (int k = 0; k < 8; ++k) { acc[k] = 0.0f; A[k] = src[k]; }
+    src += 8;
+    for (;;) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int tap = t - k;
-            if (tap >= 0 && tap <= 2 * R) {
-                const int j = tap >= R ? tap - R : R - tap;
-                acc[k] = __fmaf_rn(w[j], v, acc[k]);
-            }
-        }
+        for (int k = 0; k < 8; ++k) B[k] = src[k];
+        fma_block(acc, A, B, w4[0], w4[1]);
+        if (--nb == 0) break;
+        src += 8;
+        w4 += 2;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) A[k] = src[k];
+        fma_block(acc, B, A, w4[0], w4[1]);
+        if (--nb == 0) break;
+        src += 8;
+        w4 += 2;
     }
     float4* d4 = reinterpret_cast<float4*>(dst);
     d4[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
     d4[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
 }
 
-template <int R>
-__device__ __forceinline__ void vpass_t(const float* __restrict__ src, float* const* dst,
-                                        const float* __restrict__ wsm) {
-    float w[R + 1];
+// Vertical: inputs are rows of a circular ring of C rows (C a multiple of 8),
+// read in blocks of 8 rows starting at ring row r0; one column per lane.
+__device__ __forceinline__ void vpass(const float* __restrict__ col, int C, int r0,
+                                      const float4* __restrict__ w4, int nb, float (&acc)[8]) {
+    float A[8], B[8];
+    int r = r0;
 #pragma unroll
-    for (int j = 0; j <= R; ++j) w[j] = wsm[j];
-    float acc[8];
+    for (int k = 0; k < 8; ++k) { acc[k] = 0.0f; A[k] = col[(r + k) * RING_STRIDE]; }
+    r += 8;
+    if (r == C) r = 0;
+    for (;;) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
+        for (int k = 0; k < 8; ++k) B[k] = col[(r + k) * RING_STRIDE];
+        fma_block(acc, A, B, w4[0], w4[1]);
+        if (--nb == 0) break;
+        r += 8;
+        if (r == C) r = 0;
+        w4 += 2;
 #pragma unroll
-    for (int t = 0; t < 8 + 2 * R; ++t) {
-        const float v = src[t * RING_STRIDE];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int tap = t - k;
-            if (tap >= 0 && tap <= 2 * R) {
-                const int j = tap >= R ? tap - R : R - tap;
-                acc[k] = __fmaf_rn(w[j], v, acc[k]);
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) *dst[k] = acc[k];
-}
-
-// Radii above RT_MAX: same arithmetic order with a rolled tap loop.
-__device__ __noinline__ void hpass_g(const float* __restrict__ src, float* __restrict__ dst,
-                                     const float* __restrict__ wsm, int r) {
-    float acc[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
-    for (int t = 0; t < 8 + 2 * r; ++t) {
-        const float v = src[t];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int tap = t - k;
-            if (tap >= 0 && tap <= 2 * r) {
-                const int j = tap >= r ? tap - r : r - tap;
-                acc[k] = __fmaf_rn(wsm[j], v, acc[k]);
-            }
-        }
-    }
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    d4[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    d4[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-}
-
-__device__ __noinline__ void vpass_g(const float* __restrict__ src, float* const* dst,
-                                     const float* __restrict__ wsm, int r) {
-    float acc[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
-    for (int t = 0; t < 8 + 2 * r; ++t) {
-        const float v = src[t * RING_STRIDE];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int tap = t - k;
-            if (tap >= 0 && tap <= 2 * r) {
-                const int j = tap >= r ? tap - r : r - tap;
-                acc[k] = __fmaf_rn(wsm[j], v, acc[k]);
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) *dst[k] = acc[k];
-}
-
-#define DOG_CASES(X)                                                                      \
-    X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) \
-    X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30)  \
-    X(31) X(32) X(33) X(34) X(35) X(36) X(37) X(38) X(39) X(40) X(41) X(42) X(43) X(44)  \
-    X(45) X(46) X(47) X(48)
-
-__device__ __forceinline__ void hpass(int r, const float* src, float* dst, const float* wsm) {
-    switch (r) {
-#define DOG_H(R) \
-    case R: hpass_t<R>(src, dst, wsm); return;
-        DOG_CASES(DOG_H)
-#undef DOG_H
-        default: hpass_g(src, dst, wsm, r); return;
-    }
-}
-
-__device__ __forceinline__ void vpass(int r, const float* src, float* const* dst, const float* wsm) {
-    switch (r) {
-#define DOG_V(R) \
-    case R: vpass_t<R>(src, dst, wsm); return;
-        DOG_CASES(DOG_V)
-#undef DOG_V
-        default: vpass_g(src, dst, wsm, r); return;
+        for (int k = 0; k < 8; ++k) A[k] = col[(r + k) * RING_STRIDE];
+        fma_block(acc, B, A, w4[0], w4[1]);
+        if (--nb == 0) break;
+        r += 8;
+        if (r == C) r = 0;
+        w4 += 2;
     }
 }
 
@@ -198,6 +147,8 @@ struct SmemSmall {
     int tile;
 };
 
+__device__ __forceinline__ int dslot(int k) { return k >= DSLOTS ? k - DSLOTS : k; }
+
 __device__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc) {
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -206,7 +157,7 @@ __device__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, con
     const int P = p.P;
     const int CIN = p.in_rows;        // power of two
     const int S = p.in_stride;
-    const int ncols = TX + 2 * R;     // input columns per row
+    const int ncols = TX + 2 * R;     // input columns per row (<= NTHREADS)
     const int yb0 = tc.y0 - 1;
     const int nblk = (tc.y1 - tc.y0 + 2 + MB - 1) / MB;
     int emax = 0;
@@ -216,71 +167,51 @@ __device__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, con
     float* in = sm + p.in_off;
     float* dbuf = sm + p.d_off;
 
+    // this thread loads input column `tid` of the strip (reflected once per tile)
+    const bool loader = tid < ncols;
+    const int xsrc = loader ? refl(tc.x0 - R + tid, tc.W) : 0;
+
     // initial input rows: those read at block -emax
-    {
-        const int ya = yorg + p.dmin;
-        const int yz = yorg + p.dmax + MB;
-        const int n = (yz - ya) * ncols;
-        for (int q = tid; q < n; q += NTHREADS) {
-            const int yy = ya + q / ncols;
-            const int cc = q % ncols;
-            const float v = load_px(tc.img, tc.dtype, tc.pitch, refl(yy, tc.H), refl(tc.x0 - R + cc, tc.W));
-            in[((yy - yorg) & (CIN - 1)) * S + cc] = v;
-        }
+    for (int yy = yorg + p.dmin; yy < yorg + p.dmax + MB; ++yy) {
+        if (loader) in[((yy - yorg) & (CIN - 1)) * S + tid] = load_px(tc.img, tc.dtype, tc.pitch, refl(yy, tc.H), xsrc);
     }
     __syncthreads();
 
-    constexpr int PF = (MB * (TX + 2 * DOG_MAX_RADIUS) + NTHREADS - 1) / NTHREADS;
-    const int npf = MB * ncols;
-
     for (int b = -emax; b < nblk; ++b) {
         const int yb = yb0 + MB * b;
-        // prefetch the rows block b+1 adds (latency hidden behind phase A)
-        float pf[PF];
+        // prefetch the 8 rows block b+1 adds (latency hidden behind phase A)
+        float pf[MB];
         const int ynew = yorg + MB * (b + emax + 1) + p.dmax;
+        const bool do_pf = loader && (b + 1 < nblk);
 #pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            const int q = tid + j * NTHREADS;
-            pf[j] = 0.0f;
-            if (q < npf && b + 1 < nblk) {
-                const int yy = ynew + q / ncols;
-                const int cc = q % ncols;
-                pf[j] = load_px(tc.img, tc.dtype, tc.pitch, refl(yy, tc.H), refl(tc.x0 - R + cc, tc.W));
-            }
-        }
+        for (int j = 0; j < MB; ++j)
+            pf[j] = do_pf ? load_px(tc.img, tc.dtype, tc.pitch, refl(ynew + j, tc.H), xsrc) : 0.0f;
 
         // ---- phase A: horizontal + vertical passes of this warp's levels
         const int nl = p.warp_nlev[warp];
         for (int li = 0; li < nl; ++li) {
             const int i = p.warp_lev[warp][li];
             const LevelInfo L = p.lv[i];
-            const int c = b + L.e;
+            const int c = b + L.e;            // chunk written this block
             if (c < 0) continue;
             float* ring = sm + L.ring_off;
-            const float* wsm = sm + p.w_off + L.woff;
+            const float4* w4 = reinterpret_cast<const float4*>(sm + p.w_off + L.woff);
+            const int nb = L.tpad >> 3;
             {
                 const int rho = lane >> 2, g = lane & 3;
                 const int yy = yb + L.delta + rho;     // input row of this lane
                 const float* src = in + ((yy - yorg) & (CIN - 1)) * S + (R - L.r) + 8 * g;
-                float* dst = ring + (L.ring_rows - MB + rho) * RING_STRIDE + 8 * g;
-                hpass(L.r, src, dst, wsm);
+                const int wrow = (MB * c) % L.ring_rows + rho;
+                hpass(src, ring + wrow * RING_STRIDE + 8 * g, w4, nb);
             }
             __syncwarp();
             if (b >= 0) {
-                float* dst[8];
+                float acc[8];
+                vpass(ring + lane, L.ring_rows, (MB * b) % L.ring_rows, w4, nb, acc);
+                const int s0 = (MB * b + 2) % DSLOTS;
+                float* dcol = dbuf + i * DSLOTS * TX + lane;
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    dst[k] = dbuf + (i * DSLOTS + (MB * b + k + 2) % DSLOTS) * TX + lane;
-                vpass(L.r, ring + lane, dst, wsm);
-            }
-            __syncwarp();
-            {
-                // shift the ring up by MB rows; each (row, quad) moves within one lane
-                float4* r4 = reinterpret_cast<float4*>(ring);
-                const int rows = L.ring_rows - MB;
-                const int c4 = lane & 7;
-                for (int row = lane >> 3; row < rows; row += 4)
-                    r4[row * (RING_STRIDE / 4) + c4] = r4[(row + MB) * (RING_STRIDE / 4) + c4];
+                for (int k = 0; k < 8; ++k) dcol[dslot(s0 + k) * TX] = acc[k];
             }
             __syncwarp();
         }
@@ -294,23 +225,19 @@ __device__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, con
             const int slot = (MB * b + k + 2) % DSLOTS;
             float* col = dbuf + slot * TX + x;
             float Lnext = col[0];
+            const bool dump = (p.mode == MODE_DUMP) && y >= tc.y0 && y < tc.y1 && tc.x0 + x < tc.W;
             for (int i = 0; i < P; ++i) {
                 const float Li = Lnext;
                 Lnext = col[(i + 1) * DSLOTS * TX];
                 const float d = dog_value(ss.c[i], Li, Lnext);
                 col[i * DSLOTS * TX] = d;
-                if (p.mode == MODE_DUMP && y >= tc.y0 && y < tc.y1 && tc.x0 + x < tc.W)
-                    p.dump[((size_t)i * tc.H + y) * tc.W + tc.x0 + x] = d;
+                if (dump) p.dump[((size_t)i * tc.H + y) * tc.W + tc.x0 + x] = d;
             }
         }
-        // store the prefetched input rows (slots not read by this or the next block's old rows)
+        // store the prefetched input rows (their slots are not read before block b+1)
+        if (do_pf) {
 #pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            const int q = tid + j * NTHREADS;
-            if (q < npf && b + 1 < nblk) {
-                const int yy = ynew + q / ncols;
-                in[((yy - yorg) & (CIN - 1)) * S + q % ncols] = pf[j];
-            }
+            for (int j = 0; j < MB; ++j) in[((ynew + j - yorg) & (CIN - 1)) * S + tid] = pf[j];
         }
         __syncthreads();
 
@@ -333,7 +260,7 @@ __device__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, con
                 const float d = dbuf[(l * DSLOTS + sc) * TX + x];
                 bool cand = row_ok && col_ok && (soft || d > p.thr);
                 bool edge = false;
-                if (__any_sync(0xffffffffu, cand)) {
+                if (__ballot_sync(0xffffffffu, cand)) {
                     if (cand) {
 #pragma unroll 1
                         for (int dl = -1; dl <= 1 && cand; ++dl) {
@@ -356,65 +283,72 @@ __device__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, con
                             }
                         }
                     }
-                }
-                const bool direct = cand && !edge;
-                const bool pend = cand && edge;
-                if (p.mode == MODE_CANDIDATES) {
-                    const unsigned m = __ballot_sync(0xffffffffu, direct);
-                    if (m) {
-                        int base = 0;
-                        if (lane == 0) base = atomicAdd(tc.count, __popc(m));
-                        base = __shfl_sync(0xffffffffu, base, 0);
+                    const bool direct = cand && !edge;
+                    const bool pend = cand && edge;
+                    if (p.mode == MODE_CANDIDATES) {
+                        const unsigned m = __ballot_sync(0xffffffffu, direct);
+                        if (m) {
+                            int base = 0;
+                            if (lane == 0) base = atomicAdd(tc.count, __popc(m));
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                            if (direct) {
+                                const int idx = base + __popc(m & lanemask_lt());
+                                if (idx < p.cap) {
+                                    dog_blob bl;
+                                    bl.x = gx; bl.y = y; bl.level = l; bl.sigma = ss.sig[l]; bl.response = d;
+                                    tc.blobs[idx] = bl;
+                                } else {
+                                    atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
+                                }
+                            }
+                        }
+                    } else if (direct) {
+                        const float s = 1.0f / (1.0f + __expf(-(d - p.thr) * p.inv_T));
+                        if (p.mode == MODE_SOFT) {
+                            atomicAdd(&ss.soft[ss.kb[l][0]], s * ss.kw[l][0]);
+                            atomicAdd(&ss.soft[ss.kb[l][1]], s * ss.kw[l][1]);
+                        } else {
+                            const float G = ss.gk[l] * s * (1.0f - s) * p.inv_T;
+                            atomicAdd(&ss.dc[l], G * d / ss.c[l]);
+                            atomicAdd(&ss.dt[l], s * ss.gdk[l]);
+                        }
+                    }
+                    if (p.mode == MODE_BWD) {
+                        float G = 0.0f;
                         if (direct) {
-                            const int idx = base + __popc(m & lanemask_lt());
-                            if (idx < p.cap) {
-                                dog_blob bl;
-                                bl.x = gx; bl.y = y; bl.level = l; bl.sigma = ss.sig[l]; bl.response = d;
-                                tc.blobs[idx] = bl;
+                            const float s = 1.0f / (1.0f + __expf(-(d - p.thr) * p.inv_T));
+                            G = ss.gk[l] * s * (1.0f - s) * p.inv_T;
+                        }
+                        if (row_ok && col_ok) {
+                            const float a = ss.c[l] * G - (l > 0 ? ss.c[l - 1] * Gprev : 0.0f);
+                            p.A[((size_t)l * tc.H + y) * tc.W + gx] = a;
+                            if (l == P - 1) p.A[((size_t)(l + 1) * tc.H + y) * tc.W + gx] = -ss.c[l] * G;
+                        }
+                        Gprev = G;
+                    }
+                    const unsigned mp = __ballot_sync(0xffffffffu, pend);
+                    if (mp) {
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(p.pend_count, __popc(mp));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (pend) {
+                            const int idx = base + __popc(mp & lanemask_lt());
+                            if (idx < p.pend_cap) {
+                                Pending e;
+                                e.frame = tc.frame; e.x = gx; e.y = y; e.level = l; e.response = d;
+                                p.pend[idx] = e;
                             } else {
                                 atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
                             }
                         }
                     }
-                } else if (direct) {
-                    const float s = 1.0f / (1.0f + __expf(-(d - p.thr) * p.inv_T));
-                    if (p.mode == MODE_SOFT) {
-                        atomicAdd(&ss.soft[ss.kb[l][0]], s * ss.kw[l][0]);
-                        atomicAdd(&ss.soft[ss.kb[l][1]], s * ss.kw[l][1]);
-                    } else {
-                        const float G = ss.gk[l] * s * (1.0f - s) * p.inv_T;
-                        atomicAdd(&ss.dc[l], G * d / ss.c[l]);
-                        atomicAdd(&ss.dt[l], s * ss.gdk[l]);
-                    }
-                }
-                if (p.mode == MODE_BWD) {
-                    float G = 0.0f;
-                    if (direct) {
-                        const float s = 1.0f / (1.0f + __expf(-(d - p.thr) * p.inv_T));
-                        G = ss.gk[l] * s * (1.0f - s) * p.inv_T;
-                    }
+                } else if (p.mode == MODE_BWD) {
+                    // no voxel of this row qualifies at plane l: A = -c_{l-1} G_{l-1}
                     if (row_ok && col_ok) {
-                        const float a = ss.c[l] * G - (l > 0 ? ss.c[l - 1] * Gprev : 0.0f);
-                        p.A[((size_t)l * tc.H + y) * tc.W + gx] = a;
-                        if (l == P - 1) p.A[((size_t)(l + 1) * tc.H + y) * tc.W + gx] = -ss.c[l] * G;
+                        p.A[((size_t)l * tc.H + y) * tc.W + gx] = (l > 0 ? -ss.c[l - 1] * Gprev : 0.0f);
+                        if (l == P - 1) p.A[((size_t)(l + 1) * tc.H + y) * tc.W + gx] = 0.0f;
                     }
-                    Gprev = G;
-                }
-                const unsigned mp = __ballot_sync(0xffffffffu, pend);
-                if (mp) {
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(p.pend_count, __popc(mp));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (pend) {
-                        const int idx = base + __popc(mp & lanemask_lt());
-                        if (idx < p.pend_cap) {
-                            Pending e;
-                            e.frame = tc.frame; e.x = gx; e.y = y; e.level = l; e.response = d;
-                            p.pend[idx] = e;
-                        } else {
-                            atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
-                        }
-                    }
+                    Gprev = 0.0f;
                 }
             }
         }
@@ -428,6 +362,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
     float* sm = reinterpret_cast<float*>(dyn4);
     __shared__ SmemSmall ss;
     const int tid = threadIdx.x;
+    // zero the dynamic shared memory once: zero-weight padding taps may read
+    // input-row columns past the loaded ones, and those must be finite
+    for (int q = tid; q < p.smem_bytes / 16; q += NTHREADS) dyn4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
     for (int q = tid; q < p.w_total; q += NTHREADS) sm[p.w_off + q] = p.w[q];
     for (int q = tid; q < p.P; q += NTHREADS) ss.c[q] = p.c[q];
     for (int q = tid; q < p.P; q += NTHREADS) ss.sig[q] = 0.0f;
@@ -517,20 +455,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
     }
 }
 
+// The dynamic shared-memory limit is raised once per device and kernel form
+// (not on every launch, so launches can be captured into CUDA graphs).
+static int g_smem_limit[64][2];
+
 cudaError_t launch_fused(const FusedParams& p, int grid, cudaStream_t s) {
-    const bool batched = p.frames != nullptr;
-    cudaError_t e;
-    if (batched) {
-        e = cudaFuncSetAttribute(dog_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 p.smem_bytes);
+    const int batched = p.frames != nullptr ? 1 : 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int* lim = &g_smem_limit[dev & 63][batched];
+    if (*lim < p.smem_bytes) {
+        e = batched ? cudaFuncSetAttribute(dog_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           p.smem_bytes)
+                    : cudaFuncSetAttribute(dog_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           p.smem_bytes);
         if (e != cudaSuccess) return e;
-        dog_fused_kernel<true><<<grid, NTHREADS, p.smem_bytes, s>>>(p);
-    } else {
-        e = cudaFuncSetAttribute(dog_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 p.smem_bytes);
-        if (e != cudaSuccess) return e;
-        dog_fused_kernel<false><<<grid, NTHREADS, p.smem_bytes, s>>>(p);
+        *lim = p.smem_bytes;
     }
+    if (batched) dog_fused_kernel<true><<<grid, NTHREADS, p.smem_bytes, s>>>(p);
+    else dog_fused_kernel<false><<<grid, NTHREADS, p.smem_bytes, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -547,18 +491,13 @@ __device__ float level_value(const ResolveParams& p, const void* img, int dtype,
     for (int t = lane; t <= 2 * r; t += 32) {
         const int yy = refl(y - r + t, H);
         float acc = 0.0f;
-        for (int s = 0; s <= 2 * r; ++s) {
-            const int j = s >= r ? s - r : r - s;
-            acc = __fmaf_rn(__ldg(w + j), load_px(img, dtype, pitch, yy, refl(x - r + s, W)), acc);
-        }
+        for (int s = 0; s <= 2 * r; ++s)
+            acc = __fmaf_rn(__ldg(w + s), load_px(img, dtype, pitch, yy, refl(x - r + s, W)), acc);
         hbuf[t] = acc;
     }
     __syncwarp();
     float acc = 0.0f;
-    for (int t = 0; t <= 2 * r; ++t) {
-        const int j = t >= r ? t - r : r - t;
-        acc = __fmaf_rn(__ldg(w + j), hbuf[t], acc);
-    }
+    for (int t = 0; t <= 2 * r; ++t) acc = __fmaf_rn(__ldg(w + t), hbuf[t], acc);
     __syncwarp();
     return acc;
 }

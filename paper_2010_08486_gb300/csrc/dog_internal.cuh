@@ -29,11 +29,12 @@ enum FusedMode : int {
 
 struct LevelInfo {
     int r;          // kernel radius
-    int e;          // chunks of MB rows the ring runs ahead: ceil(2r / MB)
+    int tpad;       // taps rounded up to a multiple of 8: 8 ceil((2r+1)/8)
+    int e;          // chunks of MB rows the ring runs ahead: tpad / 8
     int delta;      // MB*e - r: input-row lead of this level's horizontal pass
     int ring_off;   // float offset of the ring in dynamic shared memory
-    int ring_rows;  // MB * (e + 1)
-    int woff;       // offset of this level's half kernel w[0..r] in the weight array
+    int ring_rows;  // tpad + 8 (circular, used in blocks of 8 rows)
+    int woff;       // offset of this level's zero-padded full kernel (tpad floats)
 };
 
 // Candidate found at a strip edge whose 3x3x3 neighbourhood crosses into the

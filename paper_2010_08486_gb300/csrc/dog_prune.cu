@@ -315,4 +315,32 @@ cudaError_t launch_ring_push(const uint32_t* hist, int nbins, uint32_t* ring, in
     return cudaGetLastError();
 }
 
+// One CTA per stream walks the batch in order and pushes that stream's frames.
+__global__ void dog_ring_push_batched_kernel(const uint32_t* hists, const int32_t* ids, int n, int nbins,
+                                             uint32_t* rings, int window, uint32_t* sums, int32_t* heads) {
+    const int sid = blockIdx.x;
+    uint32_t* ring = rings + (size_t)sid * window * nbins;
+    uint32_t* sum = sums + (size_t)sid * nbins;
+    int h = heads[sid];
+    for (int f = 0; f < n; ++f) {
+        if (ids[f] != sid) continue;
+        const int slot = h % window;
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+            const uint32_t old = (h >= window) ? ring[(size_t)slot * nbins + b] : 0u;
+            const uint32_t nw = hists[(size_t)f * nbins + b];
+            ring[(size_t)slot * nbins + b] = nw;
+            sum[b] = sum[b] - old + nw;
+        }
+        ++h;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) heads[sid] = h;
+}
+
+cudaError_t launch_ring_push_batched(const uint32_t* hists, const int32_t* ids, int n, int nbins, int n_streams,
+                                     uint32_t* rings, int window, uint32_t* sums, int32_t* heads, cudaStream_t s) {
+    dog_ring_push_batched_kernel<<<n_streams, 128, 0, s>>>(hists, ids, n, nbins, rings, window, sums, heads);
+    return cudaGetLastError();
+}
+
 }  // namespace dogk

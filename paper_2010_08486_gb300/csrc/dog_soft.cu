@@ -100,6 +100,7 @@ struct SoftPrep {
     int K, P, nbins, norm;
     int r[MAX_LEVELS];
     int woff[MAX_LEVELS];
+    int tpad[MAX_LEVELS];
     double lref0, lrefP;   // ln sigma of the reference ladder's first / last DoG plane
     float* w;
     float* dw;
@@ -125,10 +126,17 @@ __global__ void __launch_bounds__(256) soft_prep_kernel(const __grid_constant__ 
             m2 += __shfl_xor_sync(0xffffffffu, m2, o);
         }
         m2 /= z;
-        for (int j = lane; j <= r; j += 32) {
-            const double wj = exp(-(double)j * j / (2.0 * s * s)) / z;
-            p.w[p.woff[i] + j] = (float)wj;
-            p.dw[p.woff[i] + j] = (float)(wj * ((double)j * j - m2) / (s * s * s));
+        // full taps t = 0..2r (offset t - r), zero-padded to tpad
+        for (int t = lane; t < p.tpad[i]; t += 32) {
+            const int j = t - r;
+            float wv = 0.0f, dv = 0.0f;
+            if (t <= 2 * r) {
+                const double wj = exp(-(double)j * j / (2.0 * s * s)) / z;
+                wv = (float)wj;
+                dv = (float)(wj * ((double)j * j - m2) / (s * s * s));
+            }
+            p.w[p.woff[i] + t] = wv;
+            p.dw[p.woff[i] + t] = dv;
         }
     }
     for (int l = threadIdx.x; l < p.P; l += blockDim.x) {
@@ -161,6 +169,7 @@ static SoftPrep prep_params(dog_handle* h, SoftWS* ws, const float* sig) {
     for (int i = 0; i < b.K; ++i) {
         q.r[i] = b.lv[i].r;
         q.woff[i] = b.lv[i].woff;
+        q.tpad[i] = b.lv[i].tpad;
     }
     q.lref0 = std::log(ref[0]);
     q.lrefP = std::log(ref[b.P - 1]);
@@ -255,8 +264,8 @@ int soft_forward(dog_handle* h, const float* img, int H, int W, int pitch, const
 }
 
 // ---------------------------------------------------------------------------
-// 1-D adjoint of a reflect-boundary correlation with the symmetric half kernel
-// w[0..r], evaluated at index m of a line of length N with stride `st`:
+// 1-D adjoint of a reflect-boundary correlation with the symmetric full kernel
+// w[0..2r] (w[r + d] weighs offset d), evaluated at index m of a line of length N with stride `st`:
 // sum over the preimages q of m under the reflection that lie within r of the
 // line, of sum_n w[|q-n|] a[n].
 __device__ __forceinline__ float adj1d(const float* __restrict__ a, size_t st, int N, int m,
@@ -271,7 +280,7 @@ __device__ __forceinline__ float adj1d(const float* __restrict__ a, size_t st, i
         const int k = (-r - q) > 0 ? ((-r - q) + per - 1) / per : -((q + r) / per);
         for (q = q + k * per; q <= N - 1 + r; q += per) {
             const int nlo = max(0, q - r), nhi = min(N - 1, q + r);
-            for (int n = nlo; n <= nhi; ++n) acc = __fmaf_rn(__ldg(w + abs(q - n)), __ldg(a + (size_t)n * st), acc);
+            for (int n = nlo; n <= nhi; ++n) acc = __fmaf_rn(__ldg(w + r + (q - n)), __ldg(a + (size_t)n * st), acc);
         }
     }
     return acc;
@@ -333,8 +342,8 @@ __global__ void __launch_bounds__(256) adj_x_kernel(const __grid_constant__ AdjP
             const float* row = p.img + (size_t)y * p.pitch;
             for (int k = -r; k <= r; ++k) {
                 const float v = __ldg(row + refl_i(x + k, p.W));
-                hb = __fmaf_rn(__ldg(w + abs(k)), v, hb);
-                hd = __fmaf_rn(__ldg(dw + abs(k)), v, hd);
+                hb = __fmaf_rn(__ldg(w + r + k), v, hb);
+                hd = __fmaf_rn(__ldg(dw + r + k), v, hd);
             }
             const size_t o = plane * i + (size_t)y * p.W + x;
             dot = (double)p.Y[o] * (double)hd + (double)p.Yd[o] * (double)hb;

@@ -1,0 +1,95 @@
+"""Batched detection of uneven frames in one persistent launch equals the
+per-frame path, also with row bands and when replayed from a CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2010_08486_gb300 import build as libbuild
+from paper_2010_08486_gb300 import dog, synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(128, 128), (256, 512), (37, 61), (512, 512), (768, 1024), (1024, 1280), (200, 96)]
+
+
+@pytest.fixture(scope="module")
+def frames():
+    libbuild.build()
+    return [torch.from_numpy(synth.plif_frame(synth.BATCH_SEED_BASE + 1 + f, h, w)).cuda()
+            for f, (h, w) in enumerate(SIZES)]
+
+
+def per_frame(det, frames):
+    res = []
+    for img in frames:
+        blobs, hist, _ = det.detect(img)
+        torch.cuda.synchronize()
+        x, y, l, s, r = blobs.to_numpy()
+        res.append((sorted(zip(l.tolist(), y.tolist(), x.tolist(), s.tolist(), r.tolist())),
+                    hist.cpu().numpy()))
+    return res
+
+
+def unpack(det, out, counts, hists, n):
+    cap = det.cfg.blob_cap
+    c = counts.cpu().numpy()
+    res = []
+    for f in range(n):
+        x, y, l, s, r = dog.blobs_from_raw(out[f * cap:(f + 1) * cap], int(c[f]))
+        res.append((sorted(zip(l.tolist(), y.tolist(), x.tolist(), s.tolist(), r.tolist())),
+                    hists[f].cpu().numpy()))
+    return res
+
+
+def assert_same(a, b):
+    assert len(a) == len(b)
+    for (ba, ha), (bb, hb) in zip(a, b):
+        assert ba == bb
+        np.testing.assert_array_equal(ha, hb)
+
+
+def test_batched_equals_per_frame(frames):
+    det = dog.Detector(dog.plif_config(max_h=1024, max_w=1280, blob_cap=8192))
+    want = per_frame(det, frames)
+    out, counts, hists = det.detect_batched(frames)
+    torch.cuda.synchronize()
+    assert_same(unpack(det, out, counts, hists, len(frames)), want)
+    assert det.status() == 0
+    # the persistent work counter resets itself: a second launch gives the same
+    out, counts, hists = det.detect_batched(frames)
+    torch.cuda.synchronize()
+    assert_same(unpack(det, out, counts, hists, len(frames)), want)
+
+
+@pytest.mark.parametrize("band,ctas", [(64, 1), (256, 1), (128, 2)])
+def test_batched_row_bands(frames, band, ctas):
+    det = dog.Detector(dog.plif_config(max_h=1024, max_w=1280, blob_cap=8192))
+    want = per_frame(det, frames)
+    det.set_tiling(band, ctas)
+    out, counts, hists = det.detect_batched(frames)
+    torch.cuda.synchronize()
+    assert_same(unpack(det, out, counts, hists, len(frames)), want)
+
+
+def test_batched_graph_replay(frames):
+    det = dog.Detector(dog.plif_config(max_h=1024, max_w=1280, blob_cap=8192))
+    want = per_frame(det, frames)
+    table = det.frame_table(frames)
+    n = len(frames)
+    cap = det.cfg.blob_cap
+    out = torch.empty((n * cap, 5), dtype=torch.int32, device="cuda")
+    counts = torch.zeros(n, dtype=torch.int32, device="cuda")
+    hists = torch.zeros((n, det.nbins_out), dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        det.detect_batched(None, table=table, out=out, counts=counts, hists=hists, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        det.detect_batched(None, table=table, out=out, counts=counts, hists=hists, stream=s)
+    for _ in range(3):
+        out.fill_(-1)
+        counts.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert_same(unpack(det, out, counts, hists, n), want)

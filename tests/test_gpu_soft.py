@@ -1,0 +1,101 @@
+"""Differentiable form on the GPU vs the FP64 oracle: soft histogram and its
+gradient with respect to the frame and the sigma ladder.
+
+The oracle is evaluated with the GPU's own local-maximum mask (computed from
+the GPU's dumped responses with the same >= rule), so that the comparison
+isolates the arithmetic; the mask itself is pinned by the detection tests.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2010_08486_gb300 import build as libbuild
+from paper_2010_08486_gb300 import dog, synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    libbuild.build()
+
+
+def crop(seed, y0=480, x0=480, n=64):
+    return synth.plif_frame(seed)[y0:y0 + n, x0:x0 + n].copy()
+
+
+def setup(img, scale=1.0):
+    cfg = dog.grad_config(max_h=img.shape[0], max_w=img.shape[1])
+    det = dog.Detector(cfg)
+    p = parity.oracle_params(cfg)
+    sig0 = np.asarray(det.sigmas)
+    # 0.1% perturbation: the radii floor(4 sigma + 0.5) of this ladder stay fixed
+    sig = (sig0 * (1.0 + 0.001 * np.sin(np.arange(len(sig0))) * scale)).astype(np.float32)
+    return cfg, det, p, sig0, sig
+
+
+def gpu_mask(det, img_t, sig):
+    # the mask at the perturbed sigmas: a detector built on that ladder dumps D
+    cfg = dog.grad_config(sigmas=[float(s) for s in sig], max_h=img_t.shape[0], max_w=img_t.shape[1])
+    cfg.sigmas = [float(s) for s in sig]
+    d2 = dog.Detector(cfg)
+    assert d2.radii == det.radii
+    D = d2.debug_dog(img_t).cpu().numpy().astype(np.float64)
+    return oracle.max_mask(D)
+
+
+@pytest.mark.parametrize("n", [64, 200])
+def test_soft_hist_matches_oracle(n):
+    img = crop(synth.GRAD_SEED_BASE, n=n)
+    cfg, det, p, sig0, sig = setup(img)
+    t = torch.from_numpy(img).cuda()
+    s = torch.from_numpy(sig).cuda()
+    H = det.soft_hist(t, s).cpu().numpy().astype(np.float64)
+    rad = np.asarray(det.radii)
+    mask = gpu_mask(det, t, sig)
+    Ho = oracle.soft_hist(img.astype(np.float64), sig.astype(np.float64), rad, p, sig0, mask)
+    assert np.abs(H - Ho).max() <= 1e-4 * Ho.sum() + 1e-5
+    # accumulation semantics: a second call adds the same histogram again
+    H2 = det.soft_hist(t, s, out=torch.from_numpy(H.astype(np.float32)).cuda()).cpu().numpy()
+    np.testing.assert_allclose(H2, 2 * H, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("n", [64, 160])
+def test_backward_matches_oracle_gradient(n):
+    img = crop(synth.GRAD_SEED_BASE, n=n)
+    cfg, det, p, sig0, sig = setup(img)
+    t = torch.from_numpy(img).cuda()
+    s = torch.from_numpy(sig).cuda()
+    rad = np.asarray(det.radii)
+    tgt = oracle.soft_hist(crop(synth.GRAD_TARGET_SEED_BASE, n=n).astype(np.float64), sig0, rad, p, sig0)
+    mask = gpu_mask(det, t, sig)
+    Ho = oracle.soft_hist(img.astype(np.float64), sig.astype(np.float64), rad, p, sig0, mask)
+    gH = 2.0 * (Ho - tgt)
+    gi, gs = det.backward(t, s, torch.from_numpy(gH.astype(np.float32)).cuda())
+    gi, gs = gi.cpu().numpy().astype(np.float64), gs.cpu().numpy().astype(np.float64)
+    oi, osg = oracle.soft_grad(img.astype(np.float64), sig.astype(np.float64), rad, p, sig0,
+                               gH.astype(np.float32).astype(np.float64), mask)
+    assert np.linalg.norm(gi - oi) <= 1e-4 * np.linalg.norm(oi)
+    assert np.linalg.norm(gs - osg) <= 1e-4 * np.linalg.norm(osg)
+
+
+def test_autograd_function_matches_backward():
+    imgs = np.stack([crop(synth.GRAD_SEED_BASE + f, n=96) for f in range(3)])
+    cfg, det, p, sig0, sig = setup(imgs[0])
+    frames = torch.from_numpy(imgs).cuda().requires_grad_(True)
+    sigmas = torch.from_numpy(sig).cuda().requires_grad_(True)
+    target = torch.zeros(cfg.nbins, device="cuda")
+    H = dog.DoGSoftHist.apply(frames, sigmas, det)
+    loss = ((H - target) ** 2).sum()
+    loss.backward()
+    gH = (2 * (H - target)).detach()
+    gs = torch.zeros(det.K, device="cuda")
+    for b in range(3):
+        gi, _ = det.backward(frames[b].detach(), sigmas.detach(), gH, grad_sigmas=gs)
+        torch.testing.assert_close(frames.grad[b], gi, rtol=0, atol=0)
+    torch.testing.assert_close(sigmas.grad, gs, rtol=1e-6, atol=1e-6)
+    # the batch histogram is the sum of the per-frame histograms
+    Hs = sum(det.soft_hist(frames[b].detach(), sigmas.detach()) for b in range(3))
+    torch.testing.assert_close(H.detach(), Hs, rtol=1e-5, atol=1e-5)
