@@ -318,8 +318,9 @@ int dog_create(const dog_config* cfg, dog_t** out) {
     b.w_total = h->w_total;
     off += h->w_total;
     // input rows hold TX + 2R loaded columns; the padded taps of the widest
-    // level read 8 further (zero) columns; stride = 1 mod 32 for the banks
-    b.in_stride = ((TX + 2 * h->R + 8 + 31) / 32) * 32 + 1;
+    // level read 8 further (zero) columns; an odd stride keeps the eight rows
+    // read by one horizontal-pass instruction on distinct banks
+    b.in_stride = (TX + 2 * h->R + 8) | 1;
     for (int i = 0; i < h->K; ++i) {
         LevelInfo& L = b.lv[i];
         L.r = h->rad[i];
@@ -333,7 +334,9 @@ int dog_create(const dog_config* cfg, dog_t** out) {
     }
     b.dmin = dmin;
     b.dmax = dmax;
-    b.in_rows = std::max(32, ceil_pow2(dmax - dmin + MB));
+    // a block reads dmax - dmin + MB input rows; the next block's MB rows are
+    // stored while other producer warps may still read this block's
+    b.in_rows = std::max(32, ceil_pow2(dmax - dmin + 2 * MB));
     off = (off + 3) & ~3;
     b.in_off = off;
     off += b.in_rows * b.in_stride;
@@ -682,11 +685,13 @@ int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t m
     // per-frame descriptors, candidate/output offsets and the tile prefix sum
     DOG_CUDA(launch_batch_prep(d_frames, n, band, h->cand_cap, h->d_desc, h->d_cand_off, h->d_out_off,
                                h->d_hw, h->d_ntiles, s));
-    int* cand_counts = h->d_bcounts;              // n
-    int* pend_count = h->d_bcounts + n;           // 1
-    int* tile_counter = h->d_bcounts + n + 1;     // 1 (kept at zero between launches)
-    int* done_counter = h->d_bcounts + n + 2;     // 1
-    DOG_CUDA(cudaMemsetAsync(cand_counts, 0, sizeof(int) * (n + 1), s));
+    // fixed slots: the persistent kernel's work and completion counters are
+    // zero between launches (the last CTA resets them), whatever n was
+    int* tile_counter = h->d_bcounts + 0;
+    int* done_counter = h->d_bcounts + 1;
+    int* pend_count = h->d_bcounts + 2;
+    int* cand_counts = h->d_bcounts + 3;          // n
+    DOG_CUDA(cudaMemsetAsync(pend_count, 0, sizeof(int) * (n + 1), s));
     FusedParams p = h->base;
     p.frames = h->d_desc;
     p.n_frames = n;

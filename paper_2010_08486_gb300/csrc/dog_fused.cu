@@ -46,6 +46,16 @@ __device__ __forceinline__ float load_px(const void* img, int dtype, int pitch, 
     return __ldg(reinterpret_cast<const float*>(img) + (size_t)y * pitch + x);
 }
 
+// Raw load and deferred conversion (same value as load_px).
+__device__ __forceinline__ unsigned load_raw(const void* img, int dtype, int pitch, int y, int x) {
+    if (dtype == DOG_DTYPE_U16)
+        return (unsigned)__ldg(reinterpret_cast<const unsigned short*>(img) + (size_t)y * pitch + x);
+    return __float_as_uint(__ldg(reinterpret_cast<const float*>(img) + (size_t)y * pitch + x));
+}
+__device__ __forceinline__ float raw_to_px(unsigned v, int dtype) {
+    return dtype == DOG_DTYPE_U16 ? __fdiv_rn((float)v, 4095.0f) : __uint_as_float(v);
+}
+
 __device__ __forceinline__ float dog_value(float c, float a, float b) {
     return __fmul_rn(c, __fsub_rn(a, b));
 }
@@ -64,7 +74,9 @@ __device__ __forceinline__ void fma_block(float (&acc)[8], const float (&A)[8], 
 }
 
 // Horizontal: inputs are consecutive floats of one shared-memory row.
-__device__ __forceinline__ void hpass(const float* __restrict__ src, float* __restrict__ dst,
+// Output: 8 floats of one ring row, written as two float4 whose order is
+// swapped on odd rows (bank swizzle; `odd` is the ring row's parity).
+__device__ __forceinline__ void hpass(const float* __restrict__ src, float* __restrict__ dst, int odd,
                                       const float4* __restrict__ w4, int nb) {
     float acc[8], A[8], B[8];
 #pragma unroll
@@ -85,30 +97,38 @@ __device__ __forceinline__ void hpass(const float* __restrict__ src, float* __re
         w4 += 2;
     }
     float4* d4 = reinterpret_cast<float4*>(dst);
-    d4[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    d4[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    const float4 lo = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    const float4 hi = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    d4[odd] = lo;
+    d4[odd ^ 1] = hi;
 }
 
 // Vertical: inputs are rows of a circular ring of C rows (C a multiple of 8),
-// read in blocks of 8 rows starting at ring row r0; one column per lane.
-__device__ __forceinline__ void vpass(const float* __restrict__ col, int C, int r0,
+// read in blocks of 8 rows starting at ring row r0 (a multiple of 8); lane x
+// holds column x, stored at x on even rows and x ^ 4 on odd rows.
+__device__ __forceinline__ void vpass(const float* __restrict__ ring, int lane, int C, int r0,
                                       const float4* __restrict__ w4, int nb, float (&acc)[8]) {
+    const float* pe = ring + lane;
+    const float* po = ring + (lane ^ 4);
     float A[8], B[8];
     int r = r0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) { acc[k] = 0.0f; A[k] = col[(r + k) * RING_STRIDE]; }
+    for (int k = 0; k < 8; ++k) {
+        acc[k] = 0.0f;
+        A[k] = ((k & 1) ? po : pe)[(r + k) * RING_STRIDE];
+    }
     r += 8;
     if (r == C) r = 0;
     for (;;) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) B[k] = col[(r + k) * RING_STRIDE];
+        for (int k = 0; k < 8; ++k) B[k] = ((k & 1) ? po : pe)[(r + k) * RING_STRIDE];
         fma_block(acc, A, B, w4[0], w4[1]);
         if (--nb == 0) break;
         r += 8;
         if (r == C) r = 0;
         w4 += 2;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) A[k] = col[(r + k) * RING_STRIDE];
+        for (int k = 0; k < 8; ++k) A[k] = ((k & 1) ? po : pe)[(r + k) * RING_STRIDE];
         fma_block(acc, B, A, w4[0], w4[1]);
         if (--nb == 0) break;
         r += 8;
@@ -133,6 +153,26 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Named barriers (id 0 is __syncthreads).
+//   FULL:  producers arrive once a block's L rows are written; consumers wait.
+//   EMPTY: consumers arrive once a block's rows are no longer needed;
+//          producers wait before overwriting them two blocks later.
+//   PROD:  producers only, once per block (input-row visibility).
+//   CONS:  consumers only, between forming D and testing.
+// FULL and EMPTY alternate between two ids by block parity, so each id has at
+// most one generation outstanding: a producer arrives at FULL(b+2) only after
+// waiting EMPTY(b), which consumers signal after their wait on FULL(b), and
+// consumers arrive at EMPTY(b+2) only after FULL(b+2), which producers signal
+// after their wait on EMPTY(b).
+enum { BAR_FULL = 1, BAR_EMPTY = 3, BAR_PROD = 5, BAR_CONS = 6 };
+
+__device__ __forceinline__ void bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // Shared scalars of one CTA (static shared memory).
 struct SmemSmall {
     float c[MAX_LEVELS];
@@ -144,216 +184,283 @@ struct SmemSmall {
     float soft[DOG_MAX_NBINS];
     float dc[MAX_LEVELS];
     float dt[MAX_LEVELS];
+    int rpos[MAX_LEVELS];     // ring row of each level's window start
     int tile;
+    LevelInfo lv[MAX_LEVELS]; // per-level table (copied from the parameters once)
+    int wn[NWARPS];           // levels owned by each producer warp
+    unsigned char wl[NWARPS][MAX_LEVELS];
 };
 
 __device__ __forceinline__ int dslot(int k) { return k >= DSLOTS ? k - DSLOTS : k; }
 
-__device__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc) {
-    const int tid = threadIdx.x;
+// Producer warps: blur passes.  Block b's L rows go to DoG-buffer slots
+// (8b + 2 + k) mod DSLOTS.
+__device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc, int emax,
+                        int nblk) {
+    const int tid = threadIdx.x;       // 0 .. NPROD_T-1
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int R = p.R;
-    const int P = p.P;
     const int CIN = p.in_rows;        // power of two
     const int S = p.in_stride;
-    const int ncols = TX + 2 * R;     // input columns per row (<= NTHREADS)
+    const int ncols = TX + 2 * R;     // input columns per row (<= NPROD_T)
     const int yb0 = tc.y0 - 1;
-    const int nblk = (tc.y1 - tc.y0 + 2 + MB - 1) / MB;
-    int emax = 0;
-    for (int i = 0; i < p.K; ++i) emax = max(emax, p.lv[i].e);
     const int yorg = yb0 - MB * emax;   // input-ring slot origin
-
     float* in = sm + p.in_off;
     float* dbuf = sm + p.d_off;
-
-    // this thread loads input column `tid` of the strip (reflected once per tile)
     const bool loader = tid < ncols;
     const int xsrc = loader ? refl(tc.x0 - R + tid, tc.W) : 0;
 
-    // initial input rows: those read at block -emax
-    for (int yy = yorg + p.dmin; yy < yorg + p.dmax + MB; ++yy) {
-        if (loader) in[((yy - yorg) & (CIN - 1)) * S + tid] = load_px(tc.img, tc.dtype, tc.pitch, refl(yy, tc.H), xsrc);
-    }
-    __syncthreads();
-
     for (int b = -emax; b < nblk; ++b) {
         const int yb = yb0 + MB * b;
-        // prefetch the 8 rows block b+1 adds (latency hidden behind phase A)
-        float pf[MB];
+        // prefetch the 8 rows block b+1 adds (latency hidden behind the passes)
+        unsigned pf[MB];   // raw pixel bits; converted when stored, after the passes
         const int ynew = yorg + MB * (b + emax + 1) + p.dmax;
         const bool do_pf = loader && (b + 1 < nblk);
 #pragma unroll
         for (int j = 0; j < MB; ++j)
-            pf[j] = do_pf ? load_px(tc.img, tc.dtype, tc.pitch, refl(ynew + j, tc.H), xsrc) : 0.0f;
+            pf[j] = do_pf ? load_raw(tc.img, tc.dtype, tc.pitch, refl(ynew + j, tc.H), xsrc) : 0u;
+        // block b's L rows overwrite those of block b-2: wait for the consumers
+        if (b >= 2) bar_sync(BAR_EMPTY + (b & 1), NTHREADS);
 
-        // ---- phase A: horizontal + vertical passes of this warp's levels
-        const int nl = p.warp_nlev[warp];
+        const int nl = ss.wn[warp];
+        const int s0 = b >= 0 ? (MB * b + 2) % DSLOTS : 0;   // DoG-buffer slot of row yb
         for (int li = 0; li < nl; ++li) {
-            const int i = p.warp_lev[warp][li];
-            const LevelInfo L = p.lv[i];
-            const int c = b + L.e;            // chunk written this block
-            if (c < 0) continue;
-            float* ring = sm + L.ring_off;
-            const float4* w4 = reinterpret_cast<const float4*>(sm + p.w_off + L.woff);
-            const int nb = L.tpad >> 3;
-            {
-                const int rho = lane >> 2, g = lane & 3;
-                const int yy = yb + L.delta + rho;     // input row of this lane
-                const float* src = in + ((yy - yorg) & (CIN - 1)) * S + (R - L.r) + 8 * g;
-                const int wrow = (MB * c) % L.ring_rows + rho;
-                hpass(src, ring + wrow * RING_STRIDE + 8 * g, w4, nb);
-            }
-            __syncwarp();
-            if (b >= 0) {
-                float acc[8];
-                vpass(ring + lane, L.ring_rows, (MB * b) % L.ring_rows, w4, nb, acc);
-                const int s0 = (MB * b + 2) % DSLOTS;
-                float* dcol = dbuf + i * DSLOTS * TX + lane;
+            const int i = ss.wl[warp][li];
+            const LevelInfo L = ss.lv[i];
+            const int C = L.ring_rows;
+            const int r0 = ss.rpos[i];     // 8b mod C; the chunk written now goes 8 rows before
+            if (b + L.e >= 0) {
+                float* ring = sm + L.ring_off;
+                const float4* w4 = reinterpret_cast<const float4*>(sm + p.w_off + L.woff);
+                const int nb = L.tpad >> 3;
+                {
+                    const int rho = lane >> 2, g = lane & 3;
+                    const int yy = yb + L.delta + rho;     // input row of this lane
+                    const float* src = in + ((yy - yorg) & (CIN - 1)) * S + (R - L.r) + 8 * g;
+                    const int wrow = (r0 >= MB ? r0 - MB : r0 + C - MB) + rho;
+                    hpass(src, ring + wrow * RING_STRIDE + 8 * g, rho & 1, w4, nb);
+                }
+                __syncwarp();
+                if (b >= 0) {
+                    float acc[8];
+                    vpass(ring, lane, C, r0, w4, nb, acc);
+                    float* dcol = dbuf + i * DSLOTS * TX + lane;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) dcol[dslot(s0 + k) * TX] = acc[k];
+                    for (int k = 0; k < 8; ++k) dcol[dslot(s0 + k) * TX] = acc[k];
+                }
             }
             __syncwarp();
+            if (lane == 0) ss.rpos[i] = (r0 + MB == C) ? 0 : r0 + MB;
         }
-        __syncthreads();
-
-        // ---- phase B: D_i = c_i (L_i - L_{i+1}) in place for rows yb..yb+7
-        if (b >= 0) {
-            const int k = warp;
-            const int x = lane;
-            const int y = yb + k;
-            const int slot = (MB * b + k + 2) % DSLOTS;
-            float* col = dbuf + slot * TX + x;
-            float Lnext = col[0];
-            const bool dump = (p.mode == MODE_DUMP) && y >= tc.y0 && y < tc.y1 && tc.x0 + x < tc.W;
-            for (int i = 0; i < P; ++i) {
-                const float Li = Lnext;
-                Lnext = col[(i + 1) * DSLOTS * TX];
-                const float d = dog_value(ss.c[i], Li, Lnext);
-                col[i * DSLOTS * TX] = d;
-                if (dump) p.dump[((size_t)i * tc.H + y) * tc.W + tc.x0 + x] = d;
-            }
-        }
-        // store the prefetched input rows (their slots are not read before block b+1)
+        // input rows of block b+1 (their slots are not read by block b)
         if (do_pf) {
 #pragma unroll
-            for (int j = 0; j < MB; ++j) in[((ynew + j - yorg) & (CIN - 1)) * S + tid] = pf[j];
+            for (int j = 0; j < MB; ++j) in[((ynew + j - yorg) & (CIN - 1)) * S + tid] = raw_to_px(pf[j], tc.dtype);
         }
-        __syncthreads();
+        if (b >= 0) bar_arrive(BAR_FULL + (b & 1), NTHREADS);
+        bar_sync(BAR_PROD, NPROD_T);
+    }
+}
 
-        // ---- phase C: test row yb-1+warp against its 26 neighbours
-        if (b >= 0 && p.mode != MODE_DUMP) {
-            const int y = yb - 1 + warp;
-            const bool row_ok = (y >= tc.y0 && y < tc.y1);
-            const int x = lane;
-            const int gx = tc.x0 + x;
-            const bool col_ok = gx < tc.W;
-            const int sc = (MB * b + warp + 1) % DSLOTS;    // slot of row y
-            const int sm1 = (MB * b + warp) % DSLOTS;       // row y-1
-            const int sp1 = (MB * b + warp + 2) % DSLOTS;   // row y+1
-            const bool ym_ok = y - 1 >= 0, yp_ok = y + 1 < tc.H;
-            const bool left_out = (x == 0 && tc.x0 > 0);
-            const bool right_out = (x == TX - 1 && gx + 1 < tc.W);
-            const bool soft = (p.mode == MODE_SOFT || p.mode == MODE_BWD);
-            float Gprev = 0.0f;
-            for (int l = 0; l < P; ++l) {
-                const float d = dbuf[(l * DSLOTS + sc) * TX + x];
-                bool cand = row_ok && col_ok && (soft || d > p.thr);
-                bool edge = false;
-                if (__ballot_sync(0xffffffffu, cand)) {
-                    if (cand) {
+// Element l of a register array, without dynamic indexing (used on the rare
+// candidate path only).
+template <int N>
+__device__ __forceinline__ float dd_at(const float (&a)[N], int l) {
+    float v = 0.0f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) v = (j == l) ? a[j] : v;
+    return v;
+}
+
+// Consumer warps: the 3x3x3 test of rows yb-1 .. yb+6 (two rows per warp),
+// with D_l = c_l (L_l - L_{l+1}) formed on the fly from the L rows the
+// producers wrote (the DoG buffer is never rewritten).
+//
+// Per test row y and plane l: D at rows y-1, y, y+1 (three loads of L_{l+1},
+// the L_l rows carried from plane l-1), its vertical maximum, then the
+// horizontal maximum through two warp shuffles -> m_l; a voxel is a
+// candidate iff D_l(y, x) >= max(m_{l-1}, m_l, m_{l+1}) (it equals its 3x3x3
+// maximum).  Neighbours outside the frame count as -inf; those in the
+// adjacent strip are left to the resolve kernel (the candidate is queued).
+// The plane loop is unrolled over the largest ladder and predicated on the
+// real one, keeping m and D in registers; candidates are collected in a
+// per-lane bit mask and compacted afterwards (they are rare).
+__device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc, int nblk) {
+    const int cw = (threadIdx.x >> 5) - NWARPS;   // 0 .. NCONS-1
+    const int lane = threadIdx.x & 31;
+    const int P = p.P;
+    const int yb0 = tc.y0 - 1;
+    const float* dbuf = sm + p.d_off;
+    const int mode = p.mode;
+    const bool soft = (mode == MODE_SOFT || mode == MODE_BWD);
+    const float thr = p.thr;
+    const float NEG = -INFINITY;
+    const int x = lane;
+    const int gx = tc.x0 + x;
+    const bool col_ok = gx < tc.W;
+    const bool edge_x = (x == 0 && tc.x0 > 0) || (x == TX - 1 && gx + 1 < tc.W);
+    const float* colp = dbuf + x;
+    constexpr int PMAX = MAX_LEVELS - 1;
+
+    for (int b = 0; b < nblk; ++b) {
+        const int yb = yb0 + MB * b;
+        bar_sync(BAR_FULL + (b & 1), NTHREADS);
 #pragma unroll 1
-                        for (int dl = -1; dl <= 1 && cand; ++dl) {
-                            const int ll = l + dl;
-                            if (ll < 0 || ll >= P) continue;
+        for (int q = 0; q < MB / NCONS; ++q) {
+            const int w = cw * (MB / NCONS) + q;
+            const int y = yb - 1 + w;
+            const bool row_ok = (y >= tc.y0 && y < tc.y1);
+            const int sc = (MB * b + w + 1) % DSLOTS;    // slot of row y
+            const int sm1 = (MB * b + w) % DSLOTS;       // row y-1
+            const int sp1 = (MB * b + w + 2) % DSLOTS;   // row y+1
+            const bool ym_ok = y - 1 >= 0, yp_ok = y + 1 < tc.H;
+            const bool dump = (mode == MODE_DUMP) && row_ok && col_ok;
+            float mm[PMAX + 2];   // mm[l + 1] = 3x3 spatial maximum of plane l; mm[0] = mm[P + 1] = -inf
+            float dd[PMAX];       // D_l(y, x)
+            mm[0] = NEG;
+            float Lu = colp[sm1 * TX], Lc = colp[sc * TX], Ld = colp[sp1 * TX];   // L_0 rows y-1, y, y+1
 #pragma unroll
-                            for (int dy = -1; dy <= 1; ++dy) {
-                                if ((dy < 0 && !ym_ok) || (dy > 0 && !yp_ok)) continue;
-                                const int s = dy < 0 ? sm1 : (dy > 0 ? sp1 : sc);
-                                const float* row = dbuf + (ll * DSLOTS + s) * TX;
+            for (int l = 0; l < PMAX; ++l) {
+                mm[l + 1] = NEG;
+                dd[l] = 0.0f;
+                if (l < P) {
+                    const float* pl = colp + (l + 1) * DSLOTS * TX;
+                    const float nu = pl[sm1 * TX], nc = pl[sc * TX], nd = pl[sp1 * TX];
+                    const float c = ss.c[l];
+                    const float du = dog_value(c, Lu, nu), dc = dog_value(c, Lc, nc), dn = dog_value(c, Ld, nd);
+                    Lu = nu; Lc = nc; Ld = nd;
+                    dd[l] = dc;
+                    if (dump) p.dump[((size_t)l * tc.H + y) * tc.W + gx] = dc;
+                    float m = fmaxf(dc, fmaxf(ym_ok ? du : NEG, yp_ok ? dn : NEG));
+                    if (!col_ok) m = NEG;
+                    float ml = __shfl_up_sync(0xffffffffu, m, 1);
+                    float mr = __shfl_down_sync(0xffffffffu, m, 1);
+                    if (x == 0) ml = NEG;
+                    if (x == TX - 1) mr = NEG;
+                    mm[l + 1] = fmaxf(m, fmaxf(ml, mr));
+                }
+            }
+            if (mode == MODE_DUMP) continue;
+            unsigned cmask = 0u;
 #pragma unroll
-                                for (int dx = -1; dx <= 1; ++dx) {
-                                    if (dl == 0 && dy == 0 && dx == 0) continue;
-                                    const int xx = x + dx;
-                                    if (xx < 0) { edge |= left_out; continue; }
-                                    if (xx >= TX) { edge |= right_out; continue; }
-                                    if (tc.x0 + xx >= tc.W) continue;
-                                    if (row[xx] > d) cand = false;
-                                }
-                            }
-                        }
+            for (int l = 0; l < PMAX; ++l) {
+                if (l < P) {
+                    const float d = dd[l];
+                    const bool cand = d >= fmaxf(mm[l + 1], fmaxf(mm[l], mm[l + 2])) && (soft || d > thr);
+                    cmask |= cand ? (1u << l) : 0u;
+                }
+            }
+            if (!(row_ok && col_ok)) cmask = 0u;
+            const unsigned dmask = edge_x ? 0u : cmask;   // settled here
+            const unsigned pmask = edge_x ? cmask : 0u;   // queued for the resolve kernel
+            // ---- queued strip-edge candidates (lanes 0 and 31 only)
+            if (__any_sync(0xffffffffu, pmask != 0u)) {
+                unsigned rest = pmask;
+                while (rest) {
+                    const int l = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    const int idx = atomicAdd(p.pend_count, 1);
+                    if (idx < p.pend_cap) {
+                        Pending e;
+                        e.frame = tc.frame; e.x = gx; e.y = y; e.level = l; e.response = dd_at(dd, l);
+                        p.pend[idx] = e;
+                    } else {
+                        atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
                     }
-                    const bool direct = cand && !edge;
-                    const bool pend = cand && edge;
-                    if (p.mode == MODE_CANDIDATES) {
-                        const unsigned m = __ballot_sync(0xffffffffu, direct);
-                        if (m) {
-                            int base = 0;
-                            if (lane == 0) base = atomicAdd(tc.count, __popc(m));
-                            base = __shfl_sync(0xffffffffu, base, 0);
-                            if (direct) {
-                                const int idx = base + __popc(m & lanemask_lt());
-                                if (idx < p.cap) {
-                                    dog_blob bl;
-                                    bl.x = gx; bl.y = y; bl.level = l; bl.sigma = ss.sig[l]; bl.response = d;
-                                    tc.blobs[idx] = bl;
-                                } else {
-                                    atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
-                                }
-                            }
-                        }
-                    } else if (direct) {
-                        const float s = 1.0f / (1.0f + __expf(-(d - p.thr) * p.inv_T));
-                        if (p.mode == MODE_SOFT) {
-                            atomicAdd(&ss.soft[ss.kb[l][0]], s * ss.kw[l][0]);
-                            atomicAdd(&ss.soft[ss.kb[l][1]], s * ss.kw[l][1]);
+                }
+            }
+            if (mode == MODE_CANDIDATES) {
+                // one warp-wide slot reservation for all the row's candidates
+                const int nmine = __popc(dmask);
+                int incl = nmine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                if (total) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(tc.count, total);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    int idx = base + incl - nmine;
+                    unsigned rest = dmask;
+                    while (rest) {
+                        const int l = __ffs(rest) - 1;
+                        rest &= rest - 1;
+                        if (idx < p.cap) {
+                            dog_blob bl;
+                            bl.x = gx; bl.y = y; bl.level = l; bl.sigma = ss.sig[l]; bl.response = dd_at(dd, l);
+                            tc.blobs[idx] = bl;
                         } else {
-                            const float G = ss.gk[l] * s * (1.0f - s) * p.inv_T;
+                            atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
+                        }
+                        ++idx;
+                    }
+                }
+            } else if (mode == MODE_SOFT) {
+                unsigned rest = dmask;
+                while (rest) {
+                    const int l = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    const float s = 1.0f / (1.0f + __expf(-(dd_at(dd, l) - thr) * p.inv_T));
+                    atomicAdd(&ss.soft[ss.kb[l][0]], s * ss.kw[l][0]);
+                    atomicAdd(&ss.soft[ss.kb[l][1]], s * ss.kw[l][1]);
+                }
+            } else {
+                // backward prologue: dense dloss/dL rows A_l = c_l G_l - c_{l-1} G_{l-1}
+                float Gprev = 0.0f;
+#pragma unroll
+                for (int l = 0; l < PMAX; ++l) {
+                    if (l < P) {
+                        float G = 0.0f;
+                        if (dmask & (1u << l)) {
+                            const float d = dd[l];
+                            const float s = 1.0f / (1.0f + __expf(-(d - thr) * p.inv_T));
+                            G = ss.gk[l] * s * (1.0f - s) * p.inv_T;
                             atomicAdd(&ss.dc[l], G * d / ss.c[l]);
                             atomicAdd(&ss.dt[l], s * ss.gdk[l]);
                         }
-                    }
-                    if (p.mode == MODE_BWD) {
-                        float G = 0.0f;
-                        if (direct) {
-                            const float s = 1.0f / (1.0f + __expf(-(d - p.thr) * p.inv_T));
-                            G = ss.gk[l] * s * (1.0f - s) * p.inv_T;
-                        }
                         if (row_ok && col_ok) {
-                            const float a = ss.c[l] * G - (l > 0 ? ss.c[l - 1] * Gprev : 0.0f);
-                            p.A[((size_t)l * tc.H + y) * tc.W + gx] = a;
+                            p.A[((size_t)l * tc.H + y) * tc.W + gx] = ss.c[l] * G - (l > 0 ? ss.c[l - 1] * Gprev : 0.0f);
                             if (l == P - 1) p.A[((size_t)(l + 1) * tc.H + y) * tc.W + gx] = -ss.c[l] * G;
                         }
                         Gprev = G;
                     }
-                    const unsigned mp = __ballot_sync(0xffffffffu, pend);
-                    if (mp) {
-                        int base = 0;
-                        if (lane == 0) base = atomicAdd(p.pend_count, __popc(mp));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (pend) {
-                            const int idx = base + __popc(mp & lanemask_lt());
-                            if (idx < p.pend_cap) {
-                                Pending e;
-                                e.frame = tc.frame; e.x = gx; e.y = y; e.level = l; e.response = d;
-                                p.pend[idx] = e;
-                            } else {
-                                atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
-                            }
-                        }
-                    }
-                } else if (p.mode == MODE_BWD) {
-                    // no voxel of this row qualifies at plane l: A = -c_{l-1} G_{l-1}
-                    if (row_ok && col_ok) {
-                        p.A[((size_t)l * tc.H + y) * tc.W + gx] = (l > 0 ? -ss.c[l - 1] * Gprev : 0.0f);
-                        if (l == P - 1) p.A[((size_t)(l + 1) * tc.H + y) * tc.W + gx] = 0.0f;
-                    }
-                    Gprev = 0.0f;
                 }
             }
         }
-        __syncthreads();
+        // rows yb-2 .. yb+5 are free for block b+2 (arrivals match the producers' waits)
+        if (b + 2 < nblk) bar_arrive(BAR_EMPTY + (b & 1), NTHREADS);
     }
+}
+
+__device__ __forceinline__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc) {
+    const int tid = threadIdx.x;
+    const int yb0 = tc.y0 - 1;
+    const int nblk = (tc.y1 - tc.y0 + 2 + MB - 1) / MB;
+    int emax = 0;
+    for (int i = 0; i < p.K; ++i) emax = max(emax, ss.lv[i].e);
+    const int yorg = yb0 - MB * emax;
+    const int R = p.R;
+    const int ncols = TX + 2 * R;
+    // initial input rows (those read at block -emax) and ring positions 8b mod C
+    float* in = sm + p.in_off;
+    if (tid < ncols) {
+        const int xsrc = refl(tc.x0 - R + tid, tc.W);
+        for (int yy = yorg + p.dmin; yy < yorg + p.dmax + MB; ++yy)
+            in[((yy - yorg) & (p.in_rows - 1)) * p.in_stride + tid] =
+                load_px(tc.img, tc.dtype, tc.pitch, refl(yy, tc.H), xsrc);
+    }
+    for (int i = tid; i < p.K; i += NTHREADS) {
+        const int C = ss.lv[i].ring_rows;
+        ss.rpos[i] = ((-MB * emax) % C + C) % C;
+    }
+    __syncthreads();
+    if (tid < NPROD_T) produce(p, sm, ss, tc, emax, nblk);
+    else consume(p, sm, ss, tc, nblk);
+    __syncthreads();
 }
 
 template <bool BATCHED>
@@ -368,6 +475,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
     __syncthreads();
     for (int q = tid; q < p.w_total; q += NTHREADS) sm[p.w_off + q] = p.w[q];
     for (int q = tid; q < p.P; q += NTHREADS) ss.c[q] = p.c[q];
+    for (int q = tid; q < p.K; q += NTHREADS) ss.lv[q] = p.lv[q];
+    for (int q = tid; q < NWARPS * MAX_LEVELS; q += NTHREADS) ss.wl[q / MAX_LEVELS][q % MAX_LEVELS] =
+        p.warp_lev[q / MAX_LEVELS][q % MAX_LEVELS];
+    for (int q = tid; q < NWARPS; q += NTHREADS) ss.wn[q] = p.warp_nlev[q];
     for (int q = tid; q < p.P; q += NTHREADS) ss.sig[q] = 0.0f;
     if (p.mode == MODE_SOFT || p.mode == MODE_BWD) {
         for (int q = tid; q < p.nbins; q += NTHREADS) ss.soft[q] = 0.0f;

@@ -10,14 +10,17 @@ namespace dogk {
 
 // ---- fused strip kernel geometry --------------------------------------------
 // A CTA owns a strip of TX output columns and walks down a band of rows in
-// blocks of MB rows.  Eight warps each own a fixed set of scale levels.
+// blocks of MB rows.  NWARPS producer warps each own a fixed set of scale
+// levels and run the blur passes; NCONS consumer warps form the DoG and run
+// the maximum test one block behind.
 constexpr int TX = 32;
 constexpr int MB = 8;
-constexpr int NWARPS = 8;
-constexpr int NTHREADS = NWARPS * 32;
-constexpr int RING_STRIDE = 36;    // floats per row of a level's horizontal-pass ring
-constexpr int DSLOTS = MB + 2;     // rows of the DoG buffer (block + 2 rows of history)
-constexpr int RT_MAX = 48;         // radii with fully unrolled passes; larger use a loop
+constexpr int NWARPS = 8;                       // producer (blur) warps
+constexpr int NCONS = 4;                        // consumer (DoG + test) warps
+constexpr int NPROD_T = NWARPS * 32;
+constexpr int NTHREADS = (NWARPS + NCONS) * 32;
+constexpr int RING_STRIDE = 32;    // floats per ring row (bank swizzle on row parity)
+constexpr int DSLOTS = 2 * MB + 2; // DoG-buffer rows: two blocks + 2 rows of history
 constexpr int MAX_LEVELS = DOG_MAX_LEVELS;
 
 enum FusedMode : int {

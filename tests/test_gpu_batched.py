@@ -61,6 +61,17 @@ def test_batched_equals_per_frame(frames):
     assert_same(unpack(det, out, counts, hists, len(frames)), want)
 
 
+def test_batched_varying_batch_sizes_on_one_handle(frames):
+    # consecutive batched calls of different sizes reuse the handle's workspace
+    det = dog.Detector(dog.plif_config(max_h=1024, max_w=1280, blob_cap=8192))
+    want = per_frame(det, frames)
+    for sel in ([0, 1, 2, 3, 4, 5, 6], [2], [5, 0], [1, 3, 6, 4], [6]):
+        fr = [frames[i] for i in sel]
+        out, counts, hists = det.detect_batched(fr)
+        torch.cuda.synchronize()
+        assert_same(unpack(det, out, counts, hists, len(fr)), [want[i] for i in sel])
+
+
 @pytest.mark.parametrize("band,ctas", [(64, 1), (256, 1), (128, 2)])
 def test_batched_row_bands(frames, band, ctas):
     det = dog.Detector(dog.plif_config(max_h=1024, max_w=1280, blob_cap=8192))
