@@ -161,6 +161,33 @@ int dog_prune(dog_t* h, const dog_blob* d_cand, const int32_t* d_count, int32_t 
               int32_t img_h, int32_t img_w, dog_blob* d_out, int32_t cap_out, int32_t* d_nout,
               void* stream);
 
+/* Pruning without a handle and without allocating anything.  The paper has
+ * no counterpart: this is a convenience for callers that may not allocate
+ * device memory themselves, such as a plug-in whose host framework owns all
+ * device memory and forbids allocations inside its execution step, or code
+ * that runs between stream-capture calls where a cudaMalloc would break the
+ * recorded sequence.  Same result as dog_prune for the same candidate list.
+ *
+ *  h_sigmas   the n_planes DoG-plane sigmas (host, increasing), i.e. the
+ *             ladder's first K-1 values; candidate levels index them.
+ *  overlap    threshold on the normalised disc overlap, in [0, 1).
+ *  mode       DOG_PRUNE_COALESCE, DOG_PRUNE_SUPPRESS or DOG_PRUNE_OFF.
+ *  d_cand, d_count, cap_in, d_out, cap_out, d_nout   as in dog_prune.
+ *
+ * Scratch memory is a fixed array inside the library, sized for
+ * DOG_NOALLOC_MAX_CAND candidates (about 0.8 MB, held by every GPU that
+ * loads the library until the process exits): cap_in above that limit
+ * returns DOG_ERR_UNSUPPORTED.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents, so calls whose GPU work may overlap (other streams, other
+ * host threads) race: serialise them on one stream.  Overflow of cap_out is
+ * reported through *d_nout (the true count), not through a handle status. */
+#define DOG_NOALLOC_MAX_CAND 65536
+int dog_prune_noalloc(const dog_blob* d_cand, const int32_t* d_count, int32_t cap_in,
+                      const double* h_sigmas, int32_t n_planes, double overlap, int32_t mode,
+                      dog_blob* d_out, int32_t cap_out, int32_t* d_nout, void* stream);
+
 /* Blob-volume histogram (Sec. 4, Sec. 4.1 "Blobs are then histogrammed").
  * d_hist: uint32 counts (nbins, or K-1 in LADDER mode), overwritten.
  * d_hist_vol: optional (NULL ok) double sum of V per bin, overwritten.

@@ -26,11 +26,12 @@ HIST_LOGV, HIST_LADDER = 0, 1
 DTYPE_F32, DTYPE_U16 = 0, 1
 MAX_LEVELS = 32
 MAX_RADIUS = 64
+NOALLOC_MAX_CAND = 65536
 
 # Every function declared in include/dog.h, in declaration order.
 EXPORTS = (
     "dog_config_default", "dog_create", "dog_destroy", "dog_ladder", "dog_candidates", "dog_prune",
-    "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_soft_hist",
+    "dog_prune_noalloc", "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_soft_hist",
     "dog_backward", "dog_debug_dog", "dog_ring_hist_push", "dog_ring_hist_push_batched",
     "dog_profile_enable", "dog_profile_read",
     "dog_get_status", "dog_status_string",
@@ -112,6 +113,8 @@ def load(path: str | None = None):
         lib.dog_ladder.argtypes = [vp, P(i32), P(ctypes.c_double), P(i32), P(ctypes.c_double)]
         lib.dog_candidates.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp, vp]
         lib.dog_prune.argtypes = [vp, vp, vp, i32, i32, i32, vp, i32, vp, vp]
+        lib.dog_prune_noalloc.argtypes = [vp, vp, i32, P(ctypes.c_double), i32, ctypes.c_double, i32, vp, i32,
+                                          vp, vp]
         lib.dog_volume_hist.argtypes = [vp, vp, vp, i32, vp, vp, vp]
         lib.dog_detect.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp, vp, vp, vp]
         lib.dog_detect_batched.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp]

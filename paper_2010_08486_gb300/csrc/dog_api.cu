@@ -150,7 +150,11 @@ static double disc_overlap(double d, double ra, double rb) {
     return area / (M_PI * rmin * rmin);
 }
 
-static int conflict_d2(double sa, double sb, double thr) {
+namespace dogk {
+int conflict_d2(double sa, double sb, double thr);
+}
+
+int dogk::conflict_d2(double sa, double sb, double thr) {
     const double ra = std::sqrt(2.0) * sa, rb = std::sqrt(2.0) * sb;
     long long lo = 0, hi = (long long)std::ceil((ra + rb) * (ra + rb)) + 1;
     // smallest integer d2 with overlap(sqrt(d2)) <= thr; overlap is non-increasing in d2
