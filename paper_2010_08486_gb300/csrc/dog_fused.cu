@@ -73,24 +73,31 @@ __device__ __forceinline__ void fma_block(float (&acc)[8], const float (&A)[8], 
         for (int k = 0; k < 8; ++k) acc[k] = __fmaf_rn(w[u], (k + u < 8) ? A[k + u] : B[k + u - 8], acc[k]);
 }
 
-// Horizontal: inputs are consecutive floats of one shared-memory row.
-// Output: 8 floats of one ring row, written as two float4 whose order is
-// swapped on odd rows (bank swizzle; `odd` is the ring row's parity).
+// Horizontal: inputs are consecutive floats of one shared-memory row, read as
+// 16-byte vectors (src is 16-byte aligned).  Output: 8 floats of one ring
+// row, written as two float4 whose order is swapped on odd rows (bank
+// swizzle; `odd` is the ring row's parity).
+__device__ __forceinline__ void ld8(float (&v)[8], const float* __restrict__ src) {
+    const float4 a = reinterpret_cast<const float4*>(src)[0];
+    const float4 b = reinterpret_cast<const float4*>(src)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
 __device__ __forceinline__ void hpass(const float* __restrict__ src, float* __restrict__ dst, int odd,
                                       const float4* __restrict__ w4, int nb) {
     float acc[8], A[8], B[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) { acc[k] = 0.0f; A[k] = src[k]; }
+    for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
+    ld8(A, src);
     src += 8;
     for (;;) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) B[k] = src[k];
+        ld8(B, src);
         fma_block(acc, A, B, w4[0], w4[1]);
         if (--nb == 0) break;
         src += 8;
         w4 += 2;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) A[k] = src[k];
+        ld8(A, src);
         fma_block(acc, B, A, w4[0], w4[1]);
         if (--nb == 0) break;
         src += 8;
@@ -232,19 +239,19 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
             const int r0 = ss.rpos[i];     // 8b mod C; the chunk written now goes 8 rows before
             if (b + L.e >= 0) {
                 float* ring = sm + L.ring_off;
-                const float4* w4 = reinterpret_cast<const float4*>(sm + p.w_off + L.woff);
-                const int nb = L.tpad >> 3;
                 {
                     const int rho = lane >> 2, g = lane & 3;
                     const int yy = yb + L.delta + rho;     // input row of this lane
-                    const float* src = in + ((yy - yorg) & (CIN - 1)) * S + (R - L.r) + 8 * g;
+                    const float* src = in + ((yy - yorg) & (CIN - 1)) * S + L.hcol + 8 * g;
                     const int wrow = (r0 >= MB ? r0 - MB : r0 + C - MB) + rho;
-                    hpass(src, ring + wrow * RING_STRIDE + 8 * g, rho & 1, w4, nb);
+                    hpass(src, ring + wrow * RING_STRIDE + 8 * g, rho & 1,
+                          reinterpret_cast<const float4*>(sm + p.w_off + L.hoff), L.tph >> 3);
                 }
                 __syncwarp();
                 if (b >= 0) {
                     float acc[8];
-                    vpass(ring, lane, C, r0, w4, nb, acc);
+                    vpass(ring, lane, C, r0, reinterpret_cast<const float4*>(sm + p.w_off + L.woff), L.tpad >> 3,
+                          acc);
                     float* dcol = dbuf + i * DSLOTS * TX + lane;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) dcol[dslot(s0 + k) * TX] = acc[k];
@@ -277,15 +284,51 @@ __device__ __forceinline__ float dd_at(const float (&a)[N], int l) {
 // with D_l = c_l (L_l - L_{l+1}) formed on the fly from the L rows the
 // producers wrote (the DoG buffer is never rewritten).
 //
+// Plane loop of one test row y: dd[l] = D_l(y, x), mm[l + 1] = the 3x3
+// maximum of plane l around (x, y).  The vertical maximum of
+// c (L_l - L_{l+1}) over rows y-1 .. y+1 is formed as c max(L_l - L_{l+1}):
+// c > 0 and rounding is monotonic, so both are the same number.  Lanes 0 and
+// 31 receive their own value from the shuffles, which leaves their maximum
+// unchanged: neighbours outside the strip are outside the frame (-inf) or
+// settled by the resolve kernel.  EDGE: row y-1 or y+1 lies outside the
+// frame, or the strip has columns past the frame's right edge (-inf there).
+template <int PB, bool EDGE>
+__device__ __forceinline__ void test_planes(float (&mm)[PB + 2], float (&dd)[PB], const float* colp,
+                                            const float* cs, int P, int sm1, int sc, int sp1, bool ym_ok,
+                                            bool yp_ok, bool col_ok) {
+    const float NEG = -INFINITY;
+    mm[0] = NEG;
+    mm[PB + 1] = NEG;
+    float Lu = colp[sm1 * TX], Lc = colp[sc * TX], Ld = colp[sp1 * TX];   // L_0 rows y-1, y, y+1
+#pragma unroll
+    for (int l = 0; l < PB; ++l) {
+        const bool on = l < P;
+        const float* pl = colp + (on ? l + 1 : P) * DSLOTS * TX;
+        const float nu = pl[sm1 * TX], nc = pl[sc * TX], nd = pl[sp1 * TX];
+        const float c = cs[l];
+        const float eu = __fsub_rn(Lu, nu), ec = __fsub_rn(Lc, nc), en = __fsub_rn(Ld, nd);
+        Lu = nu; Lc = nc; Ld = nd;
+        dd[l] = __fmul_rn(c, ec);
+        const float e = EDGE ? fmaxf(ec, fmaxf(ym_ok ? eu : NEG, yp_ok ? en : NEG)) : fmaxf(ec, fmaxf(eu, en));
+        float m = __fmul_rn(c, e);
+        m = (EDGE ? (on && col_ok) : on) ? m : NEG;
+        const float ml = __shfl_up_sync(0xffffffffu, m, 1);
+        const float mr = __shfl_down_sync(0xffffffffu, m, 1);
+        mm[l + 1] = fmaxf(m, fmaxf(ml, mr));
+    }
+}
+
 // Per test row y and plane l: D at rows y-1, y, y+1 (three loads of L_{l+1},
 // the L_l rows carried from plane l-1), its vertical maximum, then the
 // horizontal maximum through two warp shuffles -> m_l; a voxel is a
 // candidate iff D_l(y, x) >= max(m_{l-1}, m_l, m_{l+1}) (it equals its 3x3x3
 // maximum).  Neighbours outside the frame count as -inf; those in the
 // adjacent strip are left to the resolve kernel (the candidate is queued).
-// The plane loop is unrolled over the largest ladder and predicated on the
-// real one, keeping m and D in registers; candidates are collected in a
-// per-lane bit mask and compacted afterwards (they are rare).
+// The plane loop is unrolled over PB >= P planes without branches (planes
+// l >= P read plane P and are masked to -inf), keeping m and D in registers;
+// candidates are collected in a per-lane bit mask and compacted afterwards
+// (they are rare).
+template <int PB>
 __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc, int nblk) {
     const int cw = (threadIdx.x >> 5) - NWARPS;   // 0 .. NCONS-1
     const int lane = threadIdx.x & 31;
@@ -294,14 +337,12 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
     const float* dbuf = sm + p.d_off;
     const int mode = p.mode;
     const bool soft = (mode == MODE_SOFT || mode == MODE_BWD);
-    const float thr = p.thr;
-    const float NEG = -INFINITY;
+    const float thr = soft ? -INFINITY : p.thr;   // D > thr is not applied to soft maxima
     const int x = lane;
     const int gx = tc.x0 + x;
     const bool col_ok = gx < tc.W;
     const bool edge_x = (x == 0 && tc.x0 > 0) || (x == TX - 1 && gx + 1 < tc.W);
     const float* colp = dbuf + x;
-    constexpr int PMAX = MAX_LEVELS - 1;
 
     for (int b = 0; b < nblk; ++b) {
         const int yb = yb0 + MB * b;
@@ -315,41 +356,28 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
             const int sm1 = (MB * b + w) % DSLOTS;       // row y-1
             const int sp1 = (MB * b + w + 2) % DSLOTS;   // row y+1
             const bool ym_ok = y - 1 >= 0, yp_ok = y + 1 < tc.H;
-            const bool dump = (mode == MODE_DUMP) && row_ok && col_ok;
-            float mm[PMAX + 2];   // mm[l + 1] = 3x3 spatial maximum of plane l; mm[0] = mm[P + 1] = -inf
-            float dd[PMAX];       // D_l(y, x)
-            mm[0] = NEG;
-            float Lu = colp[sm1 * TX], Lc = colp[sc * TX], Ld = colp[sp1 * TX];   // L_0 rows y-1, y, y+1
-#pragma unroll
-            for (int l = 0; l < PMAX; ++l) {
-                mm[l + 1] = NEG;
-                dd[l] = 0.0f;
-                if (l < P) {
-                    const float* pl = colp + (l + 1) * DSLOTS * TX;
-                    const float nu = pl[sm1 * TX], nc = pl[sc * TX], nd = pl[sp1 * TX];
-                    const float c = ss.c[l];
-                    const float du = dog_value(c, Lu, nu), dc = dog_value(c, Lc, nc), dn = dog_value(c, Ld, nd);
-                    Lu = nu; Lc = nc; Ld = nd;
-                    dd[l] = dc;
-                    if (dump) p.dump[((size_t)l * tc.H + y) * tc.W + gx] = dc;
-                    float m = fmaxf(dc, fmaxf(ym_ok ? du : NEG, yp_ok ? dn : NEG));
-                    if (!col_ok) m = NEG;
-                    float ml = __shfl_up_sync(0xffffffffu, m, 1);
-                    float mr = __shfl_down_sync(0xffffffffu, m, 1);
-                    if (x == 0) ml = NEG;
-                    if (x == TX - 1) mr = NEG;
-                    mm[l + 1] = fmaxf(m, fmaxf(ml, mr));
+            if (mode == MODE_DUMP) {
+                if (row_ok && col_ok) {
+                    for (int l = 0; l < P; ++l) {
+                        const float* pl = colp + l * DSLOTS * TX;
+                        p.dump[((size_t)l * tc.H + y) * tc.W + gx] =
+                            dog_value(ss.c[l], pl[sc * TX], pl[DSLOTS * TX + sc * TX]);
+                    }
                 }
+                continue;
             }
-            if (mode == MODE_DUMP) continue;
+            float mm[PB + 2];   // mm[l + 1] = 3x3 spatial maximum of plane l; mm[0] = mm[l >= P] = -inf
+            float dd[PB];       // D_l(y, x)
+            if (ym_ok && yp_ok && tc.x0 + TX <= tc.W)
+                test_planes<PB, false>(mm, dd, colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok);
+            else
+                test_planes<PB, true>(mm, dd, colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok);
             unsigned cmask = 0u;
 #pragma unroll
-            for (int l = 0; l < PMAX; ++l) {
-                if (l < P) {
-                    const float d = dd[l];
-                    const bool cand = d >= fmaxf(mm[l + 1], fmaxf(mm[l], mm[l + 2])) && (soft || d > thr);
-                    cmask |= cand ? (1u << l) : 0u;
-                }
+            for (int l = 0; l < PB; ++l) {
+                const float d = dd[l];
+                const bool cand = d >= fmaxf(mm[l + 1], fmaxf(mm[l], mm[l + 2])) && d > thr && l < P;
+                cmask |= cand ? (1u << l) : 0u;
             }
             if (!(row_ok && col_ok)) cmask = 0u;
             const unsigned dmask = edge_x ? 0u : cmask;   // settled here
@@ -404,7 +432,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                 while (rest) {
                     const int l = __ffs(rest) - 1;
                     rest &= rest - 1;
-                    const float s = 1.0f / (1.0f + __expf(-(dd_at(dd, l) - thr) * p.inv_T));
+                    const float s = 1.0f / (1.0f + __expf(-(dd_at(dd, l) - p.thr) * p.inv_T));
                     atomicAdd(&ss.soft[ss.kb[l][0]], s * ss.kw[l][0]);
                     atomicAdd(&ss.soft[ss.kb[l][1]], s * ss.kw[l][1]);
                 }
@@ -412,12 +440,12 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                 // backward prologue: dense dloss/dL rows A_l = c_l G_l - c_{l-1} G_{l-1}
                 float Gprev = 0.0f;
 #pragma unroll
-                for (int l = 0; l < PMAX; ++l) {
+                for (int l = 0; l < PB; ++l) {
                     if (l < P) {
                         float G = 0.0f;
                         if (dmask & (1u << l)) {
                             const float d = dd[l];
-                            const float s = 1.0f / (1.0f + __expf(-(d - thr) * p.inv_T));
+                            const float s = 1.0f / (1.0f + __expf(-(d - p.thr) * p.inv_T));
                             G = ss.gk[l] * s * (1.0f - s) * p.inv_T;
                             atomicAdd(&ss.dc[l], G * d / ss.c[l]);
                             atomicAdd(&ss.dt[l], s * ss.gdk[l]);
@@ -436,6 +464,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
     }
 }
 
+template <int PB>
 __device__ __forceinline__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc) {
     const int tid = threadIdx.x;
     const int yb0 = tc.y0 - 1;
@@ -459,11 +488,11 @@ __device__ __forceinline__ void process_tile(const FusedParams& p, float* sm, Sm
     }
     __syncthreads();
     if (tid < NPROD_T) produce(p, sm, ss, tc, emax, nblk);
-    else consume(p, sm, ss, tc, nblk);
+    else consume<PB>(p, sm, ss, tc, nblk);
     __syncthreads();
 }
 
-template <bool BATCHED>
+template <bool BATCHED, int PB>
 __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_constant__ FusedParams p) {
     extern __shared__ float4 dyn4[];
     float* sm = reinterpret_cast<float*>(dyn4);
@@ -474,7 +503,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
     for (int q = tid; q < p.smem_bytes / 16; q += NTHREADS) dyn4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     for (int q = tid; q < p.w_total; q += NTHREADS) sm[p.w_off + q] = p.w[q];
-    for (int q = tid; q < p.P; q += NTHREADS) ss.c[q] = p.c[q];
+    for (int q = tid; q < MAX_LEVELS; q += NTHREADS) ss.c[q] = q < p.P ? p.c[q] : 0.0f;
     for (int q = tid; q < p.K; q += NTHREADS) ss.lv[q] = p.lv[q];
     for (int q = tid; q < NWARPS * MAX_LEVELS; q += NTHREADS) ss.wl[q / MAX_LEVELS][q % MAX_LEVELS] =
         p.warp_lev[q / MAX_LEVELS][q % MAX_LEVELS];
@@ -514,7 +543,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
         tc.y1 = min(p.H, tc.y0 + p.band);
         tc.blobs = p.blobs;
         tc.count = p.count;
-        process_tile(p, sm, ss, tc);
+        process_tile<PB>(p, sm, ss, tc);
     } else {
         for (int q = tid; q < p.P; q += NTHREADS) ss.sig[q] = p.c[p.P + q];
         const long long n_tiles = p.ntiles_dev ? *p.ntiles_dev : p.n_tiles;
@@ -540,7 +569,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
             tc.y1 = min(f.h, tc.y0 + bh);
             tc.blobs = p.blobs + f.blob_off;
             tc.count = p.count + lo;
-            process_tile(p, sm, ss, tc);
+            process_tile<PB>(p, sm, ss, tc);
         }
         if (tid == 0) {
             __threadfence();
@@ -568,58 +597,60 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
 
 // The dynamic shared-memory limit is raised once per device and kernel form
 // (not on every launch, so launches can be captured into CUDA graphs).
-static int g_smem_limit[64][2];
+static int g_smem_limit[64][8];
 
-cudaError_t launch_fused(const FusedParams& p, int grid, cudaStream_t s) {
-    const int batched = p.frames != nullptr ? 1 : 0;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    int* lim = &g_smem_limit[dev & 63][batched];
+template <bool BATCHED, int PB>
+static cudaError_t launch_form(const FusedParams& p, int grid, cudaStream_t s, int* lim) {
     if (*lim < p.smem_bytes) {
-        e = batched ? cudaFuncSetAttribute(dog_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           p.smem_bytes)
-                    : cudaFuncSetAttribute(dog_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           p.smem_bytes);
+        cudaError_t e = cudaFuncSetAttribute(dog_fused_kernel<BATCHED, PB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
         if (e != cudaSuccess) return e;
         *lim = p.smem_bytes;
     }
-    if (batched) dog_fused_kernel<true><<<grid, NTHREADS, p.smem_bytes, s>>>(p);
-    else dog_fused_kernel<false><<<grid, NTHREADS, p.smem_bytes, s>>>(p);
+    dog_fused_kernel<BATCHED, PB><<<grid, NTHREADS, p.smem_bytes, s>>>(p);
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Resolve: one warp per queued strip-edge candidate.  The D values of the
-// neighbouring strip's edge column are recomputed with the fused kernel's
-// exact operation order (horizontal then vertical FMA chains from zero in
-// ascending tap order, then c * (a - b)), so they equal what that strip held.
-__device__ float level_value(const ResolveParams& p, const void* img, int dtype, int H, int W,
-                             int pitch, int m, int y, int x, float* hbuf, int lane) {
-    const int r = p.r[m];
-    const float* w = p.w + p.woff[m];
-    // horizontal chains of rows y-r .. y+r at column x
-    for (int t = lane; t <= 2 * r; t += 32) {
-        const int yy = refl(y - r + t, H);
-        float acc = 0.0f;
-        for (int s = 0; s <= 2 * r; ++s)
-            acc = __fmaf_rn(__ldg(w + s), load_px(img, dtype, pitch, yy, refl(x - r + s, W)), acc);
-        hbuf[t] = acc;
-    }
-    __syncwarp();
-    float acc = 0.0f;
-    for (int t = 0; t <= 2 * r; ++t) acc = __fmaf_rn(__ldg(w + t), hbuf[t], acc);
-    __syncwarp();
-    return acc;
+// Plane-count buckets of the consumer's unrolled test: the smallest of 8, 16,
+// 24 and MAX_LEVELS - 1 that holds P.
+template <bool BATCHED>
+static cudaError_t launch_planes(const FusedParams& p, int grid, cudaStream_t s, int* lim) {
+    if (p.P <= 8) return launch_form<BATCHED, 8>(p, grid, s, lim + 0);
+    if (p.P <= 16) return launch_form<BATCHED, 16>(p, grid, s, lim + 1);
+    if (p.P <= 24) return launch_form<BATCHED, 24>(p, grid, s, lim + 2);
+    return launch_form<BATCHED, MAX_LEVELS - 1>(p, grid, s, lim + 3);
 }
 
-__global__ void __launch_bounds__(128) dog_resolve_kernel(const __grid_constant__ ResolveParams p) {
-    __shared__ float hbuf_all[4][2 * DOG_MAX_RADIUS + 1];
-    const int warp = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    float* hbuf = hbuf_all[warp];
+cudaError_t launch_fused(const FusedParams& p, int grid, cudaStream_t s) {
+    if (p.P < 1 || p.P > MAX_LEVELS - 1) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int* lim = g_smem_limit[dev & 63];
+    return p.frames != nullptr ? launch_planes<true>(p, grid, s, lim + 4) : launch_planes<false>(p, grid, s, lim);
+}
+
+// ---------------------------------------------------------------------------
+// Resolve: one CTA per queued strip-edge candidate (grid-stride).  The D
+// values of the neighbouring strip's edge column xn are recomputed with the
+// fused kernel's exact operation order (horizontal then vertical FMA chains
+// from zero in ascending tap order, then c * (a - b)), so they equal what that
+// strip held.  The candidate needs L_m at rows y-1 .. y+1 for the levels
+// m = l-1 .. l+2; the image patch those chains read (rows y-1-Rc .. y+1+Rc,
+// columns xn-Rc .. xn+Rc, reflected; Rc the largest of the four radii) is
+// staged in shared memory once, the horizontal chains of all four levels run
+// one per thread, and twelve threads run the vertical chains.
+constexpr int RES_THREADS = 256;
+
+__host__ __device__ inline int resolve_smem_floats(int R) {
+    return (2 * R + 3) * (2 * R + 1) + 4 * (2 * R + 3) + 4 * (2 * R + 1) + 16;
+}
+
+__global__ void __launch_bounds__(RES_THREADS) dog_resolve_kernel(const __grid_constant__ ResolveParams p) {
+    extern __shared__ float rsm[];
+    const int tid = threadIdx.x;
     const int npend = min(*p.pend_count, p.pend_cap);
-    for (int q = blockIdx.x * 4 + warp; q < npend; q += gridDim.x * 4) {
+    for (int q = blockIdx.x; q < npend; q += gridDim.x) {
         const Pending e = p.pend[q];
         const void* img = p.img;
         int dtype = p.dtype, H = p.H, W = p.W, pitch = p.pitch;
@@ -633,70 +664,136 @@ __global__ void __launch_bounds__(128) dog_resolve_kernel(const __grid_constant_
         }
         const int lx = e.x % TX;
         const int xn = (lx == 0) ? e.x - 1 : e.x + 1;   // the column held by the other strip
-        bool keep = true;
         const int l = e.level;
-        // L at levels l-1 .. l+2 (those in range) and rows y-1 .. y+1
-        float Lv[4][3];
+        const int m0 = max(l - 1, 0), m1 = min(l + 2, p.K - 1);   // levels m0 .. m1
+        const int nm = m1 - m0 + 1;
+        int rr[4], off[5];
+        int Rc = 0;
+        off[0] = 0;
+#pragma unroll
         for (int mi = 0; mi < 4; ++mi) {
-            const int m = l - 1 + mi;
-            for (int yi = 0; yi < 3; ++yi) {
-                const int y = e.y - 1 + yi;
-                Lv[mi][yi] = 0.0f;
-                if (m < 0 || m >= p.K || y < 0 || y >= H) continue;
-                Lv[mi][yi] = level_value(p, img, dtype, H, W, pitch, m, y, xn, hbuf, lane);
-            }
+            rr[mi] = mi < nm ? p.r[m0 + mi] : 0;
+            Rc = max(Rc, rr[mi]);
+            off[mi + 1] = off[mi] + (mi < nm ? 2 * rr[mi] + 3 : 0);
         }
-        for (int mi = 0; mi < 3; ++mi) {
-            const int ll = l - 1 + mi;
-            if (ll < 0 || ll >= p.P) continue;
-            for (int yi = 0; yi < 3; ++yi) {
-                const int y = e.y - 1 + yi;
-                if (y < 0 || y >= H) continue;
-                const float d = __fmul_rn(__ldg(p.c + ll), __fsub_rn(Lv[mi][yi], Lv[mi + 1][yi]));
-                if (d > e.response) keep = false;
-            }
+        const int pw = 2 * Rc + 1, ph = 2 * Rc + 3;
+        float* patch = rsm;                      // ph x pw
+        float* hb = rsm + ph * pw;               // 4 x ph: horizontal sums per level
+        float* wsm = hb + 4 * ph;                // 4 x pw: taps of the four levels
+        float* Lv = wsm + 4 * pw;                // 4 x 3
+        // taps
+        for (int i = tid; i < 4 * pw; i += RES_THREADS) {
+            const int mi = i / pw, t = i - mi * pw;
+            wsm[i] = (mi < nm && t <= 2 * rr[mi]) ? __ldg(p.w + p.woff[m0 + mi] + t) : 0.0f;
         }
-        if (lane == 0 && keep) {
-            if (p.mode == MODE_CANDIDATES) {
-                const int idx = atomicAdd(count, 1);
-                if (idx < p.cap) {
-                    dog_blob bl;
-                    bl.x = e.x; bl.y = e.y; bl.level = l; bl.sigma = __ldg(p.c + p.P + l); bl.response = e.response;
-                    blobs[idx] = bl;
+        // patch: thread (row phase jt, column cc); rows jt, jt + rpp, ...
+        {
+            const int rpp = RES_THREADS / pw;
+            const int jt = tid / pw, cc = tid - jt * pw;
+            if (jt < rpp) {
+                const int xr = refl(xn - Rc + cc, W);
+                const int y0 = e.y - 1 - Rc;
+                if (dtype == DOG_DTYPE_U16) {
+                    const unsigned short* base = reinterpret_cast<const unsigned short*>(img) + xr;
+                    for (int j = jt; j < ph; j += rpp)
+                        patch[j * pw + cc] = __fdiv_rn((float)__ldg(base + (size_t)refl(y0 + j, H) * pitch), 4095.0f);
                 } else {
-                    atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
-                }
-            } else {
-                const float s = 1.0f / (1.0f + __expf(-(e.response - p.thr) * p.inv_T));
-                if (p.mode == MODE_SOFT) {
-                    for (int b = 0; b < p.nbins; ++b) {
-                        const float k = p.kappa[l * p.nbins + b];
-                        if (k != 0.0f) atomicAdd(&p.soft_out[b], s * k);
-                    }
-                } else {
-                    float gk = 0.0f, gdk = 0.0f;
-                    for (int b = 0; b < p.nbins; ++b) {
-                        gk += p.gH[b] * p.kappa[l * p.nbins + b];
-                        gdk += p.gH[b] * p.dkappa[l * p.nbins + b];
-                    }
-                    const float cl = __ldg(p.c + l);
-                    const float G = gk * s * (1.0f - s) * p.inv_T;
-                    atomicAdd(&p.A[((size_t)l * H + e.y) * W + e.x], cl * G);
-                    atomicAdd(&p.A[((size_t)(l + 1) * H + e.y) * W + e.x], -cl * G);
-                    atomicAdd(&p.dc_acc[l], (double)(G * e.response / cl));
-                    atomicAdd(&p.dt_acc[l], (double)(s * gdk));
+                    const float* base = reinterpret_cast<const float*>(img) + xr;
+                    for (int j = jt; j < ph; j += rpp)
+                        patch[j * pw + cc] = __ldg(base + (size_t)refl(y0 + j, H) * pitch);
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();
+        // horizontal chains: level mi, patch rows Rc - r .. Rc + 2 + r
+        for (int it = tid; it < off[4]; it += RES_THREADS) {
+            const int mi = (it >= off[1]) + (it >= off[2]) + (it >= off[3]);
+            const int j = it - off[mi];
+            const int r = rr[mi];
+            const float* w = wsm + mi * pw;
+            const float* src = patch + (Rc - r + j) * pw + (Rc - r);
+            float acc = 0.0f;
+#pragma unroll 8
+            for (int t = 0; t <= 2 * r; ++t) acc = __fmaf_rn(w[t], src[t], acc);
+            hb[mi * ph + j] = acc;
+        }
+        __syncthreads();
+        if (tid < 3 * nm) {
+            const int mi = tid / 3, yi = tid - 3 * mi;
+            const int r = rr[mi];
+            const float* w = wsm + mi * pw;
+            const float* src = hb + mi * ph + yi;
+            float acc = 0.0f;
+#pragma unroll 8
+            for (int t = 0; t <= 2 * r; ++t) acc = __fmaf_rn(w[t], src[t], acc);
+            Lv[mi * 3 + yi] = acc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            bool keep = true;
+            for (int ll = max(l - 1, 0); ll <= min(l + 1, p.P - 1); ++ll) {
+                for (int yi = 0; yi < 3; ++yi) {
+                    const int y = e.y - 1 + yi;
+                    if (y < 0 || y >= H) continue;
+                    const float d = __fmul_rn(__ldg(p.c + ll), __fsub_rn(Lv[(ll - m0) * 3 + yi], Lv[(ll + 1 - m0) * 3 + yi]));
+                    if (d > e.response) keep = false;
+                }
+            }
+            if (keep) {
+                if (p.mode == MODE_CANDIDATES) {
+                    const int idx = atomicAdd(count, 1);
+                    if (idx < p.cap) {
+                        dog_blob bl;
+                        bl.x = e.x; bl.y = e.y; bl.level = l; bl.sigma = __ldg(p.c + p.P + l); bl.response = e.response;
+                        blobs[idx] = bl;
+                    } else {
+                        atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
+                    }
+                } else {
+                    const float s = 1.0f / (1.0f + __expf(-(e.response - p.thr) * p.inv_T));
+                    if (p.mode == MODE_SOFT) {
+                        for (int b = 0; b < p.nbins; ++b) {
+                            const float k = p.kappa[l * p.nbins + b];
+                            if (k != 0.0f) atomicAdd(&p.soft_out[b], s * k);
+                        }
+                    } else {
+                        float gk = 0.0f, gdk = 0.0f;
+                        for (int b = 0; b < p.nbins; ++b) {
+                            gk += p.gH[b] * p.kappa[l * p.nbins + b];
+                            gdk += p.gH[b] * p.dkappa[l * p.nbins + b];
+                        }
+                        const float cl = __ldg(p.c + l);
+                        const float G = gk * s * (1.0f - s) * p.inv_T;
+                        atomicAdd(&p.A[((size_t)l * H + e.y) * W + e.x], cl * G);
+                        atomicAdd(&p.A[((size_t)(l + 1) * H + e.y) * W + e.x], -cl * G);
+                        atomicAdd(&p.dc_acc[l], (double)(G * e.response / cl));
+                        atomicAdd(&p.dt_acc[l], (double)(s * gdk));
+                    }
+                }
+            }
+        }
+        __syncthreads();   // the patch is rewritten by the next candidate
     }
 }
 
+static int g_resolve_smem[64];
+
 cudaError_t launch_resolve(const ResolveParams& p, int max_pending, cudaStream_t s) {
-    int grid = (max_pending + 3) / 4;
+    int R = 0;
+    for (int m = 0; m < p.K; ++m) R = p.r[m] > R ? p.r[m] : R;
+    const int smem = (int)sizeof(float) * resolve_smem_floats(R);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (smem > 48 * 1024 && g_resolve_smem[dev & 63] < smem) {
+        e = cudaFuncSetAttribute(dog_resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        g_resolve_smem[dev & 63] = smem;
+    }
+    int grid = max_pending;
     if (grid < 1) grid = 1;
-    if (grid > 152 * 16) grid = 152 * 16;
-    dog_resolve_kernel<<<grid, 128, 0, s>>>(p);
+    if (grid > 152 * 8) grid = 152 * 8;
+    dog_resolve_kernel<<<grid, RES_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,9 @@ struct LevelInfo {
     int ring_off;   // float offset of the ring in dynamic shared memory
     int ring_rows;  // tpad + 8 (circular, used in blocks of 8 rows)
     int woff;       // offset of this level's zero-padded full kernel (tpad floats)
+    int hoff;       // offset of its horizontal copy: `lead` zeros, the 2r+1 taps, zeros to tph
+    int tph;        // horizontal taps: 8 ceil((lead + 2r + 1) / 8)
+    int hcol;       // first input column of the horizontal pass, R - r - lead (a multiple of 4)
 };
 
 // Candidate found at a strip edge whose 3x3x3 neighbourhood crosses into the

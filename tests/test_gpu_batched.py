@@ -104,3 +104,24 @@ def test_batched_graph_replay(frames):
         g.replay()
         torch.cuda.synchronize()
         assert_same(unpack(det, out, counts, hists, n), want)
+
+
+def test_autotuned_tiling_keeps_results(frames, tmp_path):
+    from paper_2010_08486_gb300 import autotune
+    det = dog.Detector(dog.plif_config(max_h=1024, max_w=1280, blob_cap=8192))
+    want = per_frame(det, frames)
+    table = det.frame_table(frames)
+    res = autotune.tune_detector_batch(det, table, [tuple(f.shape) for f in frames],
+                                       cache_path=str(tmp_path / "tune.json"))
+    assert res.band % 8 == 0 and res.ms > 0 and len(res.timings) >= 2
+    out, counts, hists = det.detect_batched(None, table=table)
+    torch.cuda.synchronize()
+    assert_same(unpack(det, out, counts, hists, len(frames)), want)
+    # single-frame tuning on the largest frame
+    r1 = autotune.tune_detector_frame(det, frames[5])
+    blobs, hist, _ = det.detect(frames[5])
+    torch.cuda.synchronize()
+    x, y, l, s, r = blobs.to_numpy()
+    assert sorted(zip(l.tolist(), y.tolist(), x.tolist(), s.tolist(), r.tolist())) == want[5][0]
+    assert r1.band % 8 == 0
+    assert det.status() == 0
