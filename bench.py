@@ -155,8 +155,21 @@ def cpu_baseline(frames_u16, budget_s=20.0):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": n * MP_PER_FRAME / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    line = {"value": n * MP_PER_FRAME / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "%d of the workload's 1024x1024 frames through the whole path (%.1f s)" % (n, dt)}
+    # the same oracle on one core (one frame, in a child process with one OpenMP thread)
+    code = ("import sys, time, numpy as np; sys.path.insert(0, %r); import oracle; "
+            "from paper_2010_08486_gb300 import synth; "
+            "p = oracle.OracleParams(min_sigma=0.8, ratio=1.1, n_levels=25, threshold=0.05); "
+            "img = synth.u16_to_f32(synth.plif_frame_u16(synth.PLIF_SEED_BASE)).astype(np.float64); "
+            "t = time.perf_counter(); oracle.detect(img, p); print(time.perf_counter() - t)") % ROOT
+    try:
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                             env={**os.environ, "OMP_NUM_THREADS": "1"})
+        line["value_1core"] = MP_PER_FRAME / float(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        line["value_1core"] = None
+    return line
 
 
 def serve_leg(seconds, local):

@@ -73,31 +73,24 @@ __device__ __forceinline__ void fma_block(float (&acc)[8], const float (&A)[8], 
         for (int k = 0; k < 8; ++k) acc[k] = __fmaf_rn(w[u], (k + u < 8) ? A[k + u] : B[k + u - 8], acc[k]);
 }
 
-// Horizontal: inputs are consecutive floats of one shared-memory row, read as
-// 16-byte vectors (src is 16-byte aligned).  Output: 8 floats of one ring
-// row, written as two float4 whose order is swapped on odd rows (bank
-// swizzle; `odd` is the ring row's parity).
-__device__ __forceinline__ void ld8(float (&v)[8], const float* __restrict__ src) {
-    const float4 a = reinterpret_cast<const float4*>(src)[0];
-    const float4 b = reinterpret_cast<const float4*>(src)[1];
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-}
-
+// Horizontal: inputs are consecutive floats of one shared-memory row.
+// Output: 8 floats of one ring row, written as two float4 whose order is
+// swapped on odd rows (bank swizzle; `odd` is the ring row's parity).
 __device__ __forceinline__ void hpass(const float* __restrict__ src, float* __restrict__ dst, int odd,
                                       const float4* __restrict__ w4, int nb) {
     float acc[8], A[8], B[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
-    ld8(A, src);
+    for (int k = 0; k < 8; ++k) { acc[k] = 0.0f; A[k] = src[k]; }
     src += 8;
     for (;;) {
-        ld8(B, src);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) B[k] = src[k];
         fma_block(acc, A, B, w4[0], w4[1]);
         if (--nb == 0) break;
         src += 8;
         w4 += 2;
-        ld8(A, src);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) A[k] = src[k];
         fma_block(acc, B, A, w4[0], w4[1]);
         if (--nb == 0) break;
         src += 8;
@@ -239,19 +232,19 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
             const int r0 = ss.rpos[i];     // 8b mod C; the chunk written now goes 8 rows before
             if (b + L.e >= 0) {
                 float* ring = sm + L.ring_off;
+                const int nb = L.tpad >> 3;
                 {
                     const int rho = lane >> 2, g = lane & 3;
                     const int yy = yb + L.delta + rho;     // input row of this lane
-                    const float* src = in + ((yy - yorg) & (CIN - 1)) * S + L.hcol + 8 * g;
+                    const float* src = in + ((yy - yorg) & (CIN - 1)) * S + (R - L.r) + 8 * g;
                     const int wrow = (r0 >= MB ? r0 - MB : r0 + C - MB) + rho;
                     hpass(src, ring + wrow * RING_STRIDE + 8 * g, rho & 1,
-                          reinterpret_cast<const float4*>(sm + p.w_off + L.hoff), L.tph >> 3);
+                          reinterpret_cast<const float4*>(sm + p.w_off + L.hoff), nb);
                 }
                 __syncwarp();
                 if (b >= 0) {
                     float acc[8];
-                    vpass(ring, lane, C, r0, reinterpret_cast<const float4*>(sm + p.w_off + L.woff), L.tpad >> 3,
-                          acc);
+                    vpass(ring, lane, C, r0, reinterpret_cast<const float4*>(sm + p.w_off + L.woff), nb, acc);
                     float* dcol = dbuf + i * DSLOTS * TX + lane;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) dcol[dslot(s0 + k) * TX] = acc[k];
@@ -270,22 +263,16 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
     }
 }
 
-// Element l of a register array, without dynamic indexing (used on the rare
-// candidate path only).
-template <int N>
-__device__ __forceinline__ float dd_at(const float (&a)[N], int l) {
-    float v = 0.0f;
-#pragma unroll
-    for (int j = 0; j < N; ++j) v = (j == l) ? a[j] : v;
-    return v;
-}
 
 // Consumer warps: the 3x3x3 test of rows yb-1 .. yb+6 (two rows per warp),
 // with D_l = c_l (L_l - L_{l+1}) formed on the fly from the L rows the
 // producers wrote (the DoG buffer is never rewritten).
 //
-// Plane loop of one test row y: dd[l] = D_l(y, x), mm[l + 1] = the 3x3
-// maximum of plane l around (x, y).  The vertical maximum of
+// Plane loop of one test row y: returns the mask of planes l whose voxel
+// (x, y, l) is a candidate: D_l(y, x) > thr and D_l(y, x) >= m_{l-1}, m_l,
+// m_{l+1}, where m_j is the 3x3 maximum of plane j around (x, y) (-inf for
+// planes outside the ladder).  Plane l - 1 is tested as soon as m_l exists,
+// so only a window of three maxima is live.  The vertical maximum of
 // c (L_l - L_{l+1}) over rows y-1 .. y+1 is formed as c max(L_l - L_{l+1}):
 // c > 0 and rounding is monotonic, so both are the same number.  Lanes 0 and
 // 31 receive their own value from the shuffles, which leaves their maximum
@@ -293,12 +280,12 @@ __device__ __forceinline__ float dd_at(const float (&a)[N], int l) {
 // settled by the resolve kernel.  EDGE: row y-1 or y+1 lies outside the
 // frame, or the strip has columns past the frame's right edge (-inf there).
 template <int PB, bool EDGE>
-__device__ __forceinline__ void test_planes(float (&mm)[PB + 2], float (&dd)[PB], const float* colp,
-                                            const float* cs, int P, int sm1, int sc, int sp1, bool ym_ok,
-                                            bool yp_ok, bool col_ok) {
+__device__ __forceinline__ unsigned test_planes(const float* colp, const float* cs, int P, int sm1, int sc, int sp1,
+                                                bool ym_ok, bool yp_ok, bool col_ok, float thr) {
     const float NEG = -INFINITY;
-    mm[0] = NEG;
-    mm[PB + 1] = NEG;
+    float m2 = NEG, m1 = NEG;   // 3x3 maxima of planes l-2, l-1
+    float d1 = NEG;             // D_{l-1}(y, x)
+    unsigned cmask = 0u;
     float Lu = colp[sm1 * TX], Lc = colp[sc * TX], Ld = colp[sp1 * TX];   // L_0 rows y-1, y, y+1
 #pragma unroll
     for (int l = 0; l < PB; ++l) {
@@ -308,14 +295,30 @@ __device__ __forceinline__ void test_planes(float (&mm)[PB + 2], float (&dd)[PB]
         const float c = cs[l];
         const float eu = __fsub_rn(Lu, nu), ec = __fsub_rn(Lc, nc), en = __fsub_rn(Ld, nd);
         Lu = nu; Lc = nc; Ld = nd;
-        dd[l] = __fmul_rn(c, ec);
+        const float d = __fmul_rn(c, ec);
         const float e = EDGE ? fmaxf(ec, fmaxf(ym_ok ? eu : NEG, yp_ok ? en : NEG)) : fmaxf(ec, fmaxf(eu, en));
         float m = __fmul_rn(c, e);
         m = (EDGE ? (on && col_ok) : on) ? m : NEG;
         const float ml = __shfl_up_sync(0xffffffffu, m, 1);
         const float mr = __shfl_down_sync(0xffffffffu, m, 1);
-        mm[l + 1] = fmaxf(m, fmaxf(ml, mr));
+        const float m0 = fmaxf(m, fmaxf(ml, mr));
+        if (l >= 1) {
+            const bool cand = d1 >= fmaxf(m0, fmaxf(m2, m1)) && d1 > thr && l - 1 < P;
+            cmask |= cand ? (1u << (l - 1)) : 0u;
+        }
+        m2 = m1;
+        m1 = m0;
+        d1 = d;
     }
+    const bool cand = d1 >= fmaxf(m2, m1) && d1 > thr && PB - 1 < P;
+    cmask |= cand ? (1u << (PB - 1)) : 0u;
+    return cmask;
+}
+
+// D_l(y, x) of the test row (slot sc), recomputed for a candidate with the
+// operations of the plane loop.
+__device__ __forceinline__ float d_at(const float* colp, const float* cs, int l, int sc) {
+    return dog_value(cs[l], colp[l * DSLOTS * TX + sc * TX], colp[(l + 1) * DSLOTS * TX + sc * TX]);
 }
 
 // Per test row y and plane l: D at rows y-1, y, y+1 (three loads of L_{l+1},
@@ -366,19 +369,11 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                 }
                 continue;
             }
-            float mm[PB + 2];   // mm[l + 1] = 3x3 spatial maximum of plane l; mm[0] = mm[l >= P] = -inf
-            float dd[PB];       // D_l(y, x)
+            unsigned cmask;
             if (ym_ok && yp_ok && tc.x0 + TX <= tc.W)
-                test_planes<PB, false>(mm, dd, colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok);
+                cmask = test_planes<PB, false>(colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok, thr);
             else
-                test_planes<PB, true>(mm, dd, colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok);
-            unsigned cmask = 0u;
-#pragma unroll
-            for (int l = 0; l < PB; ++l) {
-                const float d = dd[l];
-                const bool cand = d >= fmaxf(mm[l + 1], fmaxf(mm[l], mm[l + 2])) && d > thr && l < P;
-                cmask |= cand ? (1u << l) : 0u;
-            }
+                cmask = test_planes<PB, true>(colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok, thr);
             if (!(row_ok && col_ok)) cmask = 0u;
             const unsigned dmask = edge_x ? 0u : cmask;   // settled here
             const unsigned pmask = edge_x ? cmask : 0u;   // queued for the resolve kernel
@@ -391,7 +386,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                     const int idx = atomicAdd(p.pend_count, 1);
                     if (idx < p.pend_cap) {
                         Pending e;
-                        e.frame = tc.frame; e.x = gx; e.y = y; e.level = l; e.response = dd_at(dd, l);
+                        e.frame = tc.frame; e.x = gx; e.y = y; e.level = l; e.response = d_at(colp, ss.c, l, sc);
                         p.pend[idx] = e;
                     } else {
                         atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
@@ -419,7 +414,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                         rest &= rest - 1;
                         if (idx < p.cap) {
                             dog_blob bl;
-                            bl.x = gx; bl.y = y; bl.level = l; bl.sigma = ss.sig[l]; bl.response = dd_at(dd, l);
+                            bl.x = gx; bl.y = y; bl.level = l; bl.sigma = ss.sig[l]; bl.response = d_at(colp, ss.c, l, sc);
                             tc.blobs[idx] = bl;
                         } else {
                             atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
@@ -432,7 +427,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                 while (rest) {
                     const int l = __ffs(rest) - 1;
                     rest &= rest - 1;
-                    const float s = 1.0f / (1.0f + __expf(-(dd_at(dd, l) - p.thr) * p.inv_T));
+                    const float s = 1.0f / (1.0f + __expf(-(d_at(colp, ss.c, l, sc) - p.thr) * p.inv_T));
                     atomicAdd(&ss.soft[ss.kb[l][0]], s * ss.kw[l][0]);
                     atomicAdd(&ss.soft[ss.kb[l][1]], s * ss.kw[l][1]);
                 }
@@ -444,7 +439,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                     if (l < P) {
                         float G = 0.0f;
                         if (dmask & (1u << l)) {
-                            const float d = dd[l];
+                            const float d = d_at(colp, ss.c, l, sc);
                             const float s = 1.0f / (1.0f + __expf(-(d - p.thr) * p.inv_T));
                             G = ss.gk[l] * s * (1.0f - s) * p.inv_T;
                             atomicAdd(&ss.dc[l], G * d / ss.c[l]);
@@ -474,13 +469,32 @@ __device__ __forceinline__ void process_tile(const FusedParams& p, float* sm, Sm
     const int yorg = yb0 - MB * emax;
     const int R = p.R;
     const int ncols = TX + 2 * R;
-    // initial input rows (those read at block -emax) and ring positions 8b mod C
+    // initial input rows (those read at block -emax), spread over all threads;
+    // each thread issues its loads before converting and storing any
     float* in = sm + p.in_off;
-    if (tid < ncols) {
-        const int xsrc = refl(tc.x0 - R + tid, tc.W);
-        for (int yy = yorg + p.dmin; yy < yorg + p.dmax + MB; ++yy)
-            in[((yy - yorg) & (p.in_rows - 1)) * p.in_stride + tid] =
-                load_px(tc.img, tc.dtype, tc.pitch, refl(yy, tc.H), xsrc);
+    {
+        const int y0 = yorg + p.dmin;
+        const int total = (p.dmax + MB - p.dmin) * ncols;
+        for (int i0 = 0; i0 < total; i0 += 8 * NTHREADS) {
+            unsigned v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * NTHREADS + tid;
+                v[u] = 0u;
+                if (i < total) {
+                    const int rr = i / ncols, cc = i - rr * ncols;
+                    v[u] = load_raw(tc.img, tc.dtype, tc.pitch, refl(y0 + rr, tc.H), refl(tc.x0 - R + cc, tc.W));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * NTHREADS + tid;
+                if (i < total) {
+                    const int rr = i / ncols, cc = i - rr * ncols;
+                    in[((y0 + rr - yorg) & (p.in_rows - 1)) * p.in_stride + cc] = raw_to_px(v[u], tc.dtype);
+                }
+            }
+        }
     }
     for (int i = tid; i < p.K; i += NTHREADS) {
         const int C = ss.lv[i].ring_rows;

@@ -22,6 +22,8 @@ constexpr int NTHREADS = (NWARPS + NCONS) * 32;
 constexpr int RING_STRIDE = 32;    // floats per ring row (bank swizzle on row parity)
 constexpr int DSLOTS = 2 * MB + 2; // DoG-buffer rows: two blocks + 2 rows of history
 constexpr int MAX_LEVELS = DOG_MAX_LEVELS;
+static_assert(MB % NCONS == 0, "each consumer warp tests whole rows of a block");
+static_assert(NTHREADS <= 1024, "one CTA");
 
 enum FusedMode : int {
     MODE_CANDIDATES = 0,  // thresholded maxima -> blob list (+ pending strip-edge list)
@@ -37,10 +39,8 @@ struct LevelInfo {
     int delta;      // MB*e - r: input-row lead of this level's horizontal pass
     int ring_off;   // float offset of the ring in dynamic shared memory
     int ring_rows;  // tpad + 8 (circular, used in blocks of 8 rows)
-    int woff;       // offset of this level's zero-padded full kernel (tpad floats)
-    int hoff;       // offset of its horizontal copy: `lead` zeros, the 2r+1 taps, zeros to tph
-    int tph;        // horizontal taps: 8 ceil((lead + 2r + 1) / 8)
-    int hcol;       // first input column of the horizontal pass, R - r - lead (a multiple of 4)
+    int woff;       // offset of this level's zero-padded full kernel (tpad floats), vertical pass
+    int hoff;       // offset of the horizontal pass's copy of the same taps
 };
 
 // Candidate found at a strip edge whose 3x3x3 neighbourhood crosses into the

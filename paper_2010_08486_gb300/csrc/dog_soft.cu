@@ -101,9 +101,7 @@ struct SoftPrep {
     int r[MAX_LEVELS];
     int woff[MAX_LEVELS];
     int tpad[MAX_LEVELS];
-    int hoff[MAX_LEVELS];    // horizontal copy: lead zeros, the taps, zeros to tph
-    int lead[MAX_LEVELS];
-    int tph[MAX_LEVELS];
+    int hoff[MAX_LEVELS];    // the horizontal pass's copy of the taps
     double lref0, lrefP;   // ln sigma of the reference ladder's first / last DoG plane
     float* w;
     float* dw;
@@ -140,17 +138,7 @@ __global__ void __launch_bounds__(256) soft_prep_kernel(const __grid_constant__ 
             }
             p.w[p.woff[i] + t] = wv;
             p.dw[p.woff[i] + t] = dv;
-        }
-        // the fused kernel's horizontal copy of the same taps
-        for (int t = lane; t < p.tph[i]; t += 32) {
-            const int u = t - p.lead[i];
-            float wv = 0.0f;
-            if (u >= 0 && u <= 2 * r) {
-                const int j = u - r;
-                wv = (float)(exp(-(double)j * j / (2.0 * s * s)) / z);
-            }
             p.w[p.hoff[i] + t] = wv;
-            p.dw[p.hoff[i] + t] = 0.0f;
         }
     }
     for (int l = threadIdx.x; l < p.P; l += blockDim.x) {
@@ -185,8 +173,6 @@ static SoftPrep prep_params(dog_handle* h, SoftWS* ws, const float* sig) {
         q.woff[i] = b.lv[i].woff;
         q.tpad[i] = b.lv[i].tpad;
         q.hoff[i] = b.lv[i].hoff;
-        q.tph[i] = b.lv[i].tph;
-        q.lead[i] = b.R - b.lv[i].r - b.lv[i].hcol;
     }
     q.lref0 = std::log(ref[0]);
     q.lrefP = std::log(ref[b.P - 1]);
