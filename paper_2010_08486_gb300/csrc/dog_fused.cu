@@ -201,25 +201,30 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int R = p.R;
-    const int CIN = p.in_rows;        // power of two
+    const int CIN = p.in_rows;        // input-buffer rows (a power of two)
     const int S = p.in_stride;
     const int ncols = TX + 2 * R;     // input columns per row (<= NPROD_T)
     const int yb0 = tc.y0 - 1;
     const int yorg = yb0 - MB * emax;   // input-ring slot origin
     float* in = sm + p.in_off;
     float* dbuf = sm + p.d_off;
-    const bool loader = tid < ncols;
-    const int xsrc = loader ? refl(tc.x0 - R + tid, tc.W) : 0;
+    // each producer warp fetches one of the MB rows a block adds (NWARPS == MB),
+    // lane x columns x, x + 32, ... of the TX + 2R loaded ones
+    static_assert(NWARPS == MB, "one prefetched row per producer warp");
+    constexpr int NPF = (TX + 2 * DOG_MAX_RADIUS + 31) / 32;
 
     for (int b = -emax; b < nblk; ++b) {
         const int yb = yb0 + MB * b;
         // prefetch the 8 rows block b+1 adds (latency hidden behind the passes)
-        unsigned pf[MB];   // raw pixel bits; converted when stored, after the passes
+        unsigned pf[NPF];   // raw pixel bits; converted when stored, after the passes
         const int ynew = yorg + MB * (b + emax + 1) + p.dmax;
-        const bool do_pf = loader && (b + 1 < nblk);
+        const bool do_pf = b + 1 < nblk;
+        const int yrow = refl(ynew + warp, tc.H);
 #pragma unroll
-        for (int j = 0; j < MB; ++j)
-            pf[j] = do_pf ? load_raw(tc.img, tc.dtype, tc.pitch, refl(ynew + j, tc.H), xsrc) : 0u;
+        for (int k = 0; k < NPF; ++k) {
+            const int cc = lane + 32 * k;
+            pf[k] = (do_pf && cc < ncols) ? load_raw(tc.img, tc.dtype, tc.pitch, yrow, refl(tc.x0 - R + cc, tc.W)) : 0u;
+        }
         // block b's L rows overwrite those of block b-2: wait for the consumers
         if (b >= 2) bar_sync(BAR_EMPTY + (b & 1), NTHREADS);
 
@@ -255,8 +260,12 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
         }
         // input rows of block b+1 (their slots are not read by block b)
         if (do_pf) {
+            float* dst = in + ((ynew + warp - yorg) & (CIN - 1)) * S;
 #pragma unroll
-            for (int j = 0; j < MB; ++j) in[((ynew + j - yorg) & (CIN - 1)) * S + tid] = raw_to_px(pf[j], tc.dtype);
+            for (int k = 0; k < NPF; ++k) {
+                const int cc = lane + 32 * k;
+                if (cc < ncols) dst[cc] = raw_to_px(pf[k], tc.dtype);
+            }
         }
         if (b >= 0) bar_arrive(BAR_FULL + (b & 1), NTHREADS);
         bar_sync(BAR_PROD, NPROD_T);
