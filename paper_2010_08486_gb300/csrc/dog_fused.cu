@@ -288,7 +288,7 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
 // unchanged: neighbours outside the strip are outside the frame (-inf) or
 // settled by the resolve kernel.  EDGE: row y-1 or y+1 lies outside the
 // frame, or the strip has columns past the frame's right edge (-inf there).
-template <int PB, bool EDGE>
+template <int PB, bool FULL, bool EDGE>
 __device__ __forceinline__ unsigned test_planes(const float* colp, const float* cs, int P, int sm1, int sc, int sp1,
                                                 bool ym_ok, bool yp_ok, bool col_ok, float thr) {
     const float NEG = -INFINITY;
@@ -298,7 +298,7 @@ __device__ __forceinline__ unsigned test_planes(const float* colp, const float* 
     float Lu = colp[sm1 * TX], Lc = colp[sc * TX], Ld = colp[sp1 * TX];   // L_0 rows y-1, y, y+1
 #pragma unroll
     for (int l = 0; l < PB; ++l) {
-        const bool on = l < P;
+        const bool on = FULL || l < P;
         const float* pl = colp + (on ? l + 1 : P) * DSLOTS * TX;
         const float nu = pl[sm1 * TX], nc = pl[sc * TX], nd = pl[sp1 * TX];
         const float c = cs[l];
@@ -312,14 +312,14 @@ __device__ __forceinline__ unsigned test_planes(const float* colp, const float* 
         const float mr = __shfl_down_sync(0xffffffffu, m, 1);
         const float m0 = fmaxf(m, fmaxf(ml, mr));
         if (l >= 1) {
-            const bool cand = d1 >= fmaxf(m0, fmaxf(m2, m1)) && d1 > thr && l - 1 < P;
+            const bool cand = d1 >= fmaxf(m0, fmaxf(m2, m1)) && d1 > thr && (FULL || l - 1 < P);
             cmask |= cand ? (1u << (l - 1)) : 0u;
         }
         m2 = m1;
         m1 = m0;
         d1 = d;
     }
-    const bool cand = d1 >= fmaxf(m2, m1) && d1 > thr && PB - 1 < P;
+    const bool cand = d1 >= fmaxf(m2, m1) && d1 > thr && (FULL || PB - 1 < P);
     cmask |= cand ? (1u << (PB - 1)) : 0u;
     return cmask;
 }
@@ -340,7 +340,7 @@ __device__ __forceinline__ float d_at(const float* colp, const float* cs, int l,
 // l >= P read plane P and are masked to -inf), keeping m and D in registers;
 // candidates are collected in a per-lane bit mask and compacted afterwards
 // (they are rare).
-template <int PB>
+template <int PB, bool FULL>
 __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc, int nblk) {
     const int cw = (threadIdx.x >> 5) - NWARPS;   // 0 .. NCONS-1
     const int lane = threadIdx.x & 31;
@@ -380,9 +380,9 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
             }
             unsigned cmask;
             if (ym_ok && yp_ok && tc.x0 + TX <= tc.W)
-                cmask = test_planes<PB, false>(colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok, thr);
+                cmask = test_planes<PB, FULL, false>(colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok, thr);
             else
-                cmask = test_planes<PB, true>(colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok, thr);
+                cmask = test_planes<PB, FULL, true>(colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok, thr);
             if (!(row_ok && col_ok)) cmask = 0u;
             const unsigned dmask = edge_x ? 0u : cmask;   // settled here
             const unsigned pmask = edge_x ? cmask : 0u;   // queued for the resolve kernel
@@ -468,7 +468,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
     }
 }
 
-template <int PB>
+template <int PB, bool FULL>
 __device__ __forceinline__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc) {
     const int tid = threadIdx.x;
     const int yb0 = tc.y0 - 1;
@@ -511,11 +511,11 @@ __device__ __forceinline__ void process_tile(const FusedParams& p, float* sm, Sm
     }
     __syncthreads();
     if (tid < NPROD_T) produce(p, sm, ss, tc, emax, nblk);
-    else consume<PB>(p, sm, ss, tc, nblk);
+    else consume<PB, FULL>(p, sm, ss, tc, nblk);
     __syncthreads();
 }
 
-template <bool BATCHED, int PB>
+template <bool BATCHED, int PB, bool FULL>
 __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_constant__ FusedParams p) {
     extern __shared__ float4 dyn4[];
     float* sm = reinterpret_cast<float*>(dyn4);
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
         tc.y1 = min(p.H, tc.y0 + p.band);
         tc.blobs = p.blobs;
         tc.count = p.count;
-        process_tile<PB>(p, sm, ss, tc);
+        process_tile<PB, FULL>(p, sm, ss, tc);
     } else {
         for (int q = tid; q < p.P; q += NTHREADS) ss.sig[q] = p.c[p.P + q];
         const long long n_tiles = p.ntiles_dev ? *p.ntiles_dev : p.n_tiles;
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
             tc.y1 = min(f.h, tc.y0 + bh);
             tc.blobs = p.blobs + f.blob_off;
             tc.count = p.count + lo;
-            process_tile<PB>(p, sm, ss, tc);
+            process_tile<PB, FULL>(p, sm, ss, tc);
         }
         if (tid == 0) {
             __threadfence();
@@ -620,28 +620,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
 
 // The dynamic shared-memory limit is raised once per device and kernel form
 // (not on every launch, so launches can be captured into CUDA graphs).
-static int g_smem_limit[64][8];
+static int g_smem_limit[64][16];
 
-template <bool BATCHED, int PB>
+template <bool BATCHED, int PB, bool FULL>
 static cudaError_t launch_form(const FusedParams& p, int grid, cudaStream_t s, int* lim) {
     if (*lim < p.smem_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(dog_fused_kernel<BATCHED, PB>,
+        cudaError_t e = cudaFuncSetAttribute(dog_fused_kernel<BATCHED, PB, FULL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
         if (e != cudaSuccess) return e;
         *lim = p.smem_bytes;
     }
-    dog_fused_kernel<BATCHED, PB><<<grid, NTHREADS, p.smem_bytes, s>>>(p);
+    dog_fused_kernel<BATCHED, PB, FULL><<<grid, NTHREADS, p.smem_bytes, s>>>(p);
     return cudaGetLastError();
 }
 
+template <bool BATCHED, int PB>
+static cudaError_t launch_bucket(const FusedParams& p, int grid, cudaStream_t s, int* lim) {
+    return p.P == PB ? launch_form<BATCHED, PB, true>(p, grid, s, lim + 1)
+                     : launch_form<BATCHED, PB, false>(p, grid, s, lim);
+}
+
 // Plane-count buckets of the consumer's unrolled test: the smallest of 8, 16,
-// 24 and MAX_LEVELS - 1 that holds P.
+// 24 and MAX_LEVELS - 1 that holds P; a ladder that fills its bucket exactly
+// runs a form without the masks of planes past the ladder.
 template <bool BATCHED>
 static cudaError_t launch_planes(const FusedParams& p, int grid, cudaStream_t s, int* lim) {
-    if (p.P <= 8) return launch_form<BATCHED, 8>(p, grid, s, lim + 0);
-    if (p.P <= 16) return launch_form<BATCHED, 16>(p, grid, s, lim + 1);
-    if (p.P <= 24) return launch_form<BATCHED, 24>(p, grid, s, lim + 2);
-    return launch_form<BATCHED, MAX_LEVELS - 1>(p, grid, s, lim + 3);
+    if (p.P <= 8) return launch_bucket<BATCHED, 8>(p, grid, s, lim + 0);
+    if (p.P <= 16) return launch_bucket<BATCHED, 16>(p, grid, s, lim + 2);
+    if (p.P <= 24) return launch_bucket<BATCHED, 24>(p, grid, s, lim + 4);
+    return launch_bucket<BATCHED, MAX_LEVELS - 1>(p, grid, s, lim + 6);
 }
 
 cudaError_t launch_fused(const FusedParams& p, int grid, cudaStream_t s) {
@@ -650,7 +657,7 @@ cudaError_t launch_fused(const FusedParams& p, int grid, cudaStream_t s) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     int* lim = g_smem_limit[dev & 63];
-    return p.frames != nullptr ? launch_planes<true>(p, grid, s, lim + 4) : launch_planes<false>(p, grid, s, lim);
+    return p.frames != nullptr ? launch_planes<true>(p, grid, s, lim + 8) : launch_planes<false>(p, grid, s, lim);
 }
 
 // ---------------------------------------------------------------------------
