@@ -64,8 +64,15 @@ __device__ __forceinline__ int neighbour_buckets(int cx, int cy, unsigned* bk) {
     return nb;
 }
 
+// Frames with at most PRUNE_SMEM_CAND candidates run every pass on
+// shared-memory copies of the candidates and the per-candidate arrays
+// (dynamic shared memory, PRUNE_DYN_BYTES); larger ones work in global memory.
+constexpr int PRUNE_SMEM_CAND = 4096;
+constexpr int PRUNE_DYN_BYTES = PRUNE_SMEM_CAND * ((int)sizeof(dog_blob) + 3 * (int)sizeof(int));
+
 __global__ void __launch_bounds__(PRUNE_THREADS) dog_prune_kernel(const __grid_constant__ PruneParams p) {
     __shared__ PruneSmem s;
+    extern __shared__ int4 prune_dyn[];
     const int f = blockIdx.x;
     const int tid = threadIdx.x;
     const long long coff = p.cand_off ? p.cand_off[f] : 0;
@@ -76,6 +83,16 @@ __global__ void __launch_bounds__(PRUNE_THREADS) dog_prune_kernel(const __grid_c
     int* order = p.order + coff;
     dog_blob* out = p.out + ooff;
     const int n = min(p.cand_count[f], p.cap_in);
+    if (n <= PRUNE_SMEM_CAND && p.mode != DOG_PRUNE_OFF) {
+        dog_blob* sc = reinterpret_cast<dog_blob*>(prune_dyn);
+        int* si = reinterpret_cast<int*>(sc + PRUNE_SMEM_CAND);
+        for (int i = tid; i < n; i += PRUNE_THREADS) sc[i] = cand[i];
+        cand = sc;
+        state = si;
+        target = si + PRUNE_SMEM_CAND;
+        order = si + 2 * PRUNE_SMEM_CAND;
+        // made visible by the first __syncthreads below
+    }
 
     if (p.mode == DOG_PRUNE_OFF) {
         for (int i = tid; i < n; i += PRUNE_THREADS) {
@@ -236,8 +253,18 @@ __global__ void __launch_bounds__(PRUNE_THREADS) dog_prune_kernel(const __grid_c
     }
 }
 
+static bool g_prune_attr[64];
+
 cudaError_t launch_prune(const PruneParams& p, cudaStream_t s) {
-    dog_prune_kernel<<<p.n_frames, PRUNE_THREADS, 0, s>>>(p);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (!g_prune_attr[dev & 63]) {   // once per device, so launches can be graph-captured
+        e = cudaFuncSetAttribute(dog_prune_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PRUNE_DYN_BYTES);
+        if (e != cudaSuccess) return e;
+        g_prune_attr[dev & 63] = true;
+    }
+    dog_prune_kernel<<<p.n_frames, PRUNE_THREADS, PRUNE_DYN_BYTES, s>>>(p);
     return cudaGetLastError();
 }
 
