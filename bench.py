@@ -260,26 +260,35 @@ def batched_leg(local, cache_path, reps=5):
         ms_b = _events_ms(g.replay, reps, s)
     torch.cuda.synchronize()
     c_batched = counts.cpu().clone()
-    # the plain path: one dog_detect per frame, whole-frame tiles
-    det.set_tiling(0)
+    # the plain path: one dog_detect per frame, with the band height tuned for
+    # each frame size
+    bands = {}
+    for f in range(n):
+        shp = tuple(frames[f].shape)
+        if shp not in bands:
+            det.set_tiling(0)
+            bands[shp] = autotune.tune_detector_frame(det, frames[f], cache_path=cache_path).band
     blobs = dog.empty_blobs(cap, "cuda")
     hist1 = torch.zeros(det.nbins_out, dtype=torch.int32, device="cuda")
     c_single = torch.zeros(n, dtype=torch.int32)
 
     def per_frame():
         for f in range(n):
+            det.set_tiling(bands[tuple(frames[f].shape)])
             det.detect(frames[f], out=blobs, hist=hist1, stream=s)
     with torch.cuda.stream(s):
         per_frame()
         torch.cuda.synchronize()
         ms_p = _events_ms(per_frame, 2, s)
         for f in range(n):   # counts of the plain path (same frames)
+            det.set_tiling(bands[tuple(frames[f].shape)])
             det.detect(frames[f], out=blobs, hist=hist1, stream=s)
             c_single[f] = int(blobs.count.item())
     assert det.status() == 0
     return {"frames": n, "megapixels": round(mp_total, 3), "band_rows": tuned.band,
             "graph_replay_ms": ms_b, "mp_per_s": mp_total / (ms_b / 1e3),
             "per_frame_ms": ms_p, "per_frame_mp_per_s": mp_total / (ms_p / 1e3),
+            "per_frame_band_rows": {"%dx%d" % k: v for k, v in sorted(bands.items())},
             "speedup_vs_per_frame": ms_p / ms_b,
             "same_blob_counts_as_per_frame": bool(torch.equal(c_batched, c_single)),
             "dtype": "f32"}
@@ -296,6 +305,8 @@ def diff_leg(local, reps=3):
     arrs = _pool_frames(synth.plif_frame, [(synth.GRAD_SEED_BASE + f, 1024, 1024) for f in range(B)])
     frames = torch.from_numpy(np.stack(arrs)).cuda()
     det = dog.Detector(dog.grad_config())
+    from paper_2010_08486_gb300 import autotune
+    tuned = autotune.tune_detector_frame(det, frames[0])   # row bands for 1024^2 frames, this ladder
     sig0 = torch.tensor([1.25 ** k for k in range(12)], dtype=torch.float32, device="cuda")
     with torch.no_grad():
         tgt_frames = torch.from_numpy(np.stack(_pool_frames(
@@ -322,7 +333,7 @@ def diff_leg(local, reps=3):
     fwd()
     ms_f = _events_ms(fwd, reps, s)
     mp = B * 1024 * 1024 / 1e6
-    return {"frames": B, "sigmas": 12, "fwd_bwd_ms": ms, "mp_per_s": mp / (ms / 1e3),
+    return {"frames": B, "sigmas": 12, "band_rows": tuned.band, "fwd_bwd_ms": ms, "mp_per_s": mp / (ms / 1e3),
             "plain_detect_ms": ms_f, "plain_mp_per_s": mp / (ms_f / 1e3), "ratio_to_plain": ms / ms_f,
             "dtype": "f32 (f64 sigma-gradient sums)"}
 

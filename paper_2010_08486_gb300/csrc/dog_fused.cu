@@ -697,15 +697,17 @@ __global__ void __launch_bounds__(RES_THREADS) dog_resolve_kernel(const __grid_c
         const int l = e.level;
         const int m0 = max(l - 1, 0), m1 = min(l + 2, p.K - 1);   // levels m0 .. m1
         const int nm = m1 - m0 + 1;
-        int rr[4], off[5];
-        int Rc = 0;
-        off[0] = 0;
-#pragma unroll
-        for (int mi = 0; mi < 4; ++mi) {
-            rr[mi] = mi < nm ? p.r[m0 + mi] : 0;
-            Rc = max(Rc, rr[mi]);
-            off[mi + 1] = off[mi] + (mi < nm ? 2 * rr[mi] + 3 : 0);
-        }
+        // radii of the (up to) four levels and the prefix offsets of their
+        // horizontal chains, in named scalars (no dynamically indexed arrays)
+        const int ra = p.r[m0];
+        const int rb = nm > 1 ? p.r[m0 + 1] : 0;
+        const int rc = nm > 2 ? p.r[m0 + 2] : 0;
+        const int rd = nm > 3 ? p.r[m0 + 3] : 0;
+        const int Rc = max(max(ra, rb), max(rc, rd));
+        const int o1 = 2 * ra + 3;
+        const int o2 = o1 + (nm > 1 ? 2 * rb + 3 : 0);
+        const int o3 = o2 + (nm > 2 ? 2 * rc + 3 : 0);
+        const int o4 = o3 + (nm > 3 ? 2 * rd + 3 : 0);
         const int pw = 2 * Rc + 1, ph = 2 * Rc + 3;
         float* patch = rsm;                      // ph x pw
         float* hb = rsm + ph * pw;               // 4 x ph: horizontal sums per level
@@ -714,32 +716,38 @@ __global__ void __launch_bounds__(RES_THREADS) dog_resolve_kernel(const __grid_c
         // taps
         for (int i = tid; i < 4 * pw; i += RES_THREADS) {
             const int mi = i / pw, t = i - mi * pw;
-            wsm[i] = (mi < nm && t <= 2 * rr[mi]) ? __ldg(p.w + p.woff[m0 + mi] + t) : 0.0f;
+            const int r = mi == 0 ? ra : (mi == 1 ? rb : (mi == 2 ? rc : rd));
+            wsm[i] = (mi < nm && t <= 2 * r) ? __ldg(p.w + p.woff[m0 + mi] + t) : 0.0f;
         }
-        // patch: thread (row phase jt, column cc); rows jt, jt + rpp, ...
+        // patch: thread (row phase jt, column cc); rows jt, jt + rpp, ...; the
+        // loads of four rows are issued before any is converted
         {
             const int rpp = RES_THREADS / pw;
             const int jt = tid / pw, cc = tid - jt * pw;
             if (jt < rpp) {
                 const int xr = refl(xn - Rc + cc, W);
                 const int y0 = e.y - 1 - Rc;
-                if (dtype == DOG_DTYPE_U16) {
-                    const unsigned short* base = reinterpret_cast<const unsigned short*>(img) + xr;
-                    for (int j = jt; j < ph; j += rpp)
-                        patch[j * pw + cc] = __fdiv_rn((float)__ldg(base + (size_t)refl(y0 + j, H) * pitch), 4095.0f);
-                } else {
-                    const float* base = reinterpret_cast<const float*>(img) + xr;
-                    for (int j = jt; j < ph; j += rpp)
-                        patch[j * pw + cc] = __ldg(base + (size_t)refl(y0 + j, H) * pitch);
+                for (int j = jt; j < ph; j += 4 * rpp) {
+                    unsigned v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int jj = j + u * rpp;
+                        v[u] = jj < ph ? load_raw(img, dtype, pitch, refl(y0 + jj, H), xr) : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int jj = j + u * rpp;
+                        if (jj < ph) patch[jj * pw + cc] = raw_to_px(v[u], dtype);
+                    }
                 }
             }
         }
         __syncthreads();
         // horizontal chains: level mi, patch rows Rc - r .. Rc + 2 + r
-        for (int it = tid; it < off[4]; it += RES_THREADS) {
-            const int mi = (it >= off[1]) + (it >= off[2]) + (it >= off[3]);
-            const int j = it - off[mi];
-            const int r = rr[mi];
+        for (int it = tid; it < o4; it += RES_THREADS) {
+            const int mi = (it >= o1) + (it >= o2) + (it >= o3);
+            const int j = it - (mi == 0 ? 0 : (mi == 1 ? o1 : (mi == 2 ? o2 : o3)));
+            const int r = mi == 0 ? ra : (mi == 1 ? rb : (mi == 2 ? rc : rd));
             const float* w = wsm + mi * pw;
             const float* src = patch + (Rc - r + j) * pw + (Rc - r);
             float acc = 0.0f;
@@ -750,7 +758,7 @@ __global__ void __launch_bounds__(RES_THREADS) dog_resolve_kernel(const __grid_c
         __syncthreads();
         if (tid < 3 * nm) {
             const int mi = tid / 3, yi = tid - 3 * mi;
-            const int r = rr[mi];
+            const int r = mi == 0 ? ra : (mi == 1 ? rb : (mi == 2 ? rc : rd));
             const float* w = wsm + mi * pw;
             const float* src = hb + mi * ph + yi;
             float acc = 0.0f;

@@ -49,18 +49,15 @@ struct PruneSmem {
     int scan_carry;
 };
 
-// Collect the distinct buckets of the 3x3 cells around (cx, cy).
+// The buckets of the 3x3 cells around (cx, cy).  Two cells may hash to the
+// same bucket; every use below is unaffected by visiting a candidate twice
+// (an any-of test, a maximum, a search for the next member in priority order).
 __device__ __forceinline__ int neighbour_buckets(int cx, int cy, unsigned* bk) {
     int nb = 0;
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-            const unsigned b = bucket_of(cx + dx, cy + dy);
-            bool dup = false;
-            for (int q = 0; q < nb; ++q) dup |= (bk[q] == b);
-            if (!dup) bk[nb++] = b;
-        }
+        for (int dx = -1; dx <= 1; ++dx) bk[nb++] = bucket_of(cx + dx, cy + dy);
     return nb;
 }
 
@@ -169,9 +166,11 @@ __global__ void __launch_bounds__(PRUNE_THREADS) dog_prune_kernel(const __grid_c
             if (vstate[i] != ST_UND) continue;
             const dog_blob bi = cand[i];
             unsigned bk[9];
-            const int nb = neighbour_buckets(bi.x / cell, bi.y / cell, bk);
+            neighbour_buckets(bi.x / cell, bi.y / cell, bk);
             bool any_in = false, any_und = false;
-            for (int q = 0; q < nb && !any_in; ++q) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                if (any_in) break;
                 for (int k = s.boff[bk[q]]; k < s.boff[bk[q] + 1]; ++k) {
                     const int j = order[k];
                     if (j == i) continue;
@@ -198,12 +197,13 @@ __global__ void __launch_bounds__(PRUNE_THREADS) dog_prune_kernel(const __grid_c
         if (state[i] != ST_OUT) continue;
         const dog_blob bi = cand[i];
         unsigned bk[9];
-        const int nb = neighbour_buckets(bi.x / cell, bi.y / cell, bk);
+        neighbour_buckets(bi.x / cell, bi.y / cell, bk);
         int best = -1;
-        for (int q = 0; q < nb; ++q)
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
             for (int k = s.boff[bk[q]]; k < s.boff[bk[q] + 1]; ++k) {
                 const int j = order[k];
-                if (j == i || state[j] != ST_IN) continue;
+                if (j == i || (state[j] & 3) != ST_IN) continue;
                 const dog_blob bj = cand[j];
                 const int dx = bj.x - bi.x, dy = bj.y - bi.y;
                 if (dx * dx + dy * dy >= s.d2[plane_of(bi, p.P) * p.P + plane_of(bj, p.P)]) continue;
@@ -212,24 +212,27 @@ __global__ void __launch_bounds__(PRUNE_THREADS) dog_prune_kernel(const __grid_c
             }
         target[i] = best;
         if (best < 0) atomicCAS(p.status, 0, (int)DOG_ERR_INVALID);   // cannot happen
+        else atomicAdd(&state[best], 4);   // member count of an accepted candidate, above the state bits
     }
     __syncthreads();
 
     // 4. accepted blobs: group mean sigma summed in visiting order, then compaction
     for (int a = tid; a < n; a += PRUNE_THREADS) {
-        if (state[a] != ST_IN) continue;
+        if ((state[a] & 3) != ST_IN) continue;
+        const int nmem = state[a] >> 2;
         const dog_blob ba = cand[a];
         double sum = p.sig[plane_of(ba, p.P)];
         int cnt = 1;
         bool mixed = false;
-        if (p.mode == DOG_PRUNE_COALESCE) {
+        if (p.mode == DOG_PRUNE_COALESCE && nmem > 0) {
             unsigned bk[9];
-            const int nb = neighbour_buckets(ba.x / cell, ba.y / cell, bk);
+            neighbour_buckets(ba.x / cell, ba.y / cell, bk);
             int prev = a;
             for (;;) {
                 // next member after `prev` in priority order
                 int nxt = -1;
-                for (int q = 0; q < nb; ++q)
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
                     for (int k = s.boff[bk[q]]; k < s.boff[bk[q] + 1]; ++k) {
                         const int j = order[k];
                         if (target[j] != a) continue;
@@ -243,6 +246,7 @@ __global__ void __launch_bounds__(PRUNE_THREADS) dog_prune_kernel(const __grid_c
                 ++cnt;
                 mixed |= (bn.level != ba.level);
                 prev = nxt;
+                if (cnt > nmem) break;   // all members visited
             }
         }
         dog_blob o = ba;

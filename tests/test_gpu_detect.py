@@ -221,3 +221,22 @@ def test_detect_recovers_isolated_blobs_at_known_radius():
         lev, sg, resp = got[c]
         assert lev == j and sg == np.float32(det.sigmas[j])
         assert abs(resp - 0.8 / 2.1) < 1e-3 * 0.8 / 2.1
+
+
+def test_prune_many_candidates_global_path():
+    """More candidates than the pruning kernel copies to shared memory (4096):
+    it then works on the global arrays; the result is the oracle's prune of the
+    same candidate list."""
+    cfg = dog.plif_config(threshold=0.0, max_h=512, max_w=512)
+    img = synth.plif_frame(synth.PLIF_SEED_BASE + 7, 512, 512)
+    det = dog.Detector(cfg)
+    cand, (x, y, l, s, r) = gpu_candidates(det, dev(img))
+    assert len(x) > 4096
+    pr = det.prune(cand, 512, 512)
+    torch.cuda.synchronize()
+    p = parity.oracle_params(cfg)
+    gpu_pr = parity.blobs_to_oracle(*pr.to_numpy())
+    ora_pr = oracle.prune(parity.blobs_to_oracle(x, y, l, s, r), p)
+    ora_pr.sigma = ora_pr.sigma.astype(np.float32).astype(np.float64)
+    assert parity.same_blob_sets(gpu_pr, ora_pr), "prune differs"
+    assert det.status() == 0
