@@ -466,24 +466,42 @@ def run_ours(a):
     if clk_s:
         line["clocks"] = clk_s
 
-    # end to end through the public API: pinned host frames in, histograms and counts out
+    # end to end through the public API: pinned host frames in, histograms and
+    # counts out, every step.  Two device frame buffers: the copy of step i+1's
+    # frames (copy stream) overlaps step i's detection (compute stream).
     if not a.no_e2e:
         counts_h = torch.zeros_like(counts, device="cpu").pin_memory()
         hists_h = torch.zeros_like(hists, device="cpu").pin_memory()
+        bufs = [frames, torch.empty_like(frames)]
+        tabs = [table, det.frame_table([bufs[1][i] for i in range(B)], cap)]
+        cstream = torch.cuda.Stream()
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        freed = [torch.cuda.Event(), torch.cuda.Event()]
 
-        def e2e_step():
-            frames.copy_(host, non_blocking=True)
-            step()
-            counts_h.copy_(counts, non_blocking=True)
-            hists_h.copy_(hists, non_blocking=True)
+        def run_e2e(nsteps):
+            cstream.wait_stream(stream)
+            with torch.cuda.stream(cstream):
+                bufs[0].copy_(host, non_blocking=True)
+                copied[0].record(cstream)
+            for i in range(nsteps):
+                k = i % 2
+                if i + 1 < nsteps:
+                    with torch.cuda.stream(cstream):
+                        if i >= 1:
+                            cstream.wait_event(freed[1 - k])   # step i-1 is done with that buffer
+                        bufs[1 - k].copy_(host, non_blocking=True)
+                        copied[1 - k].record(cstream)
+                stream.wait_event(copied[k])
+                det.detect_batched(None, table=tabs[k], out=out, counts=counts, hists=hists, stream=stream)
+                freed[k].record(stream)
+                counts_h.copy_(counts, non_blocking=True)
+                hists_h.copy_(hists, non_blocking=True)
 
-        for _ in range(a.warmup):
-            e2e_step()
+        run_e2e(a.warmup)
         torch.cuda.synchronize()
         barrier()
         ev0.record(stream)
-        for _ in range(a.steps):
-            e2e_step()
+        run_e2e(a.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
         e_ms = ev0.elapsed_time(ev1)
@@ -493,7 +511,8 @@ def run_ours(a):
             e_ms = float(t.item())
         line["e2e"] = {"value": world * B * a.steps * MP_PER_FRAME / (e_ms / 1000.0), "unit": UNIT,
                        "h2d_bytes_per_step": int(host.numel() * host.element_size()),
-                       "d2h_bytes_per_step": int(counts.numel() * 4 + hists.numel() * 4)}
+                       "d2h_bytes_per_step": int(counts.numel() * 4 + hists.numel() * 4),
+                       "pipelining": "step i+1's host-to-device copy overlaps step i's detection"}
 
     # per-frame latency: one frame at a time through dog_detect, autotuned row bands
     det.set_tiling(0)

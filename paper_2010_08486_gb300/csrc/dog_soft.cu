@@ -16,6 +16,7 @@
 // writes A densely; the adjoint blurs gather through the reflect fold-back.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -303,63 +304,213 @@ struct AdjParams {
     const float* img;
     int pitch;
     float* gimg;
-    int H, W, K;
+    int H, W, K, R;
     const float* w;
     const float* dw;
     int r[MAX_LEVELS];
+    int tpad[MAX_LEVELS];
     int woff[MAX_LEVELS];
     double* dw_acc;
 };
 
-// Column adjoint of every level: Y_i = B_y^T A_i (kernel w_i), Yd_i (kernel dw_i).
+// Tiled adjoints.  Both kernels of a level, w(t) and dw/dsigma(t), are even
+// in t, so away from the frame's edges the adjoint of a blur is the same
+// correlation: out(m) = sum_{u < Tpad} k[u] X(m - r + u) over zero-padded taps.
+// Eight consecutive outputs per thread are accumulated against a two-window
+// register file (8 inputs per block of 8 taps), for two tap sets at once.
+// Outputs within r of an edge, where the reflect boundary folds the sums, take
+// the exact preimage gather (adj1d).
+__device__ __forceinline__ void tap_block2(float (&o)[8], float (&od)[8], const float (&A)[8], const float (&B)[8],
+                                           const float* __restrict__ w, const float* __restrict__ dw) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const float a = w[u], b = dw[u];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float x = (k + u < 8) ? A[k + u] : B[k + u - 8];
+            o[k] = __fmaf_rn(a, x, o[k]);
+            od[k] = __fmaf_rn(b, x, od[k]);
+        }
+    }
+}
+
+// out[k] = sum_u w[u] X[(k + u) st], od[k] with dw; u < 8 nb.
+__device__ __forceinline__ void corr8x2(const float* __restrict__ X, int st, const float* __restrict__ w,
+                                        const float* __restrict__ dw, int nb, float (&o)[8], float (&od)[8]) {
+    float A[8], B[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        o[k] = 0.0f;
+        od[k] = 0.0f;
+        A[k] = X[k * st];
+    }
+    int j = 0;
+    for (;;) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) B[k] = X[(8 * j + 8 + k) * st];
+        tap_block2(o, od, A, B, w + 8 * j, dw + 8 * j);
+        if (++j == nb) break;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) A[k] = X[(8 * j + 8 + k) * st];
+        tap_block2(o, od, B, A, w + 8 * j, dw + 8 * j);
+        if (++j == nb) break;
+    }
+}
+
+// One tap set: out[k] = sum_u w[u] X[(k + u) st], u < 8 nb.
+__device__ __forceinline__ void corr8(const float* __restrict__ X, int st, const float* __restrict__ w, int nb,
+                                      float (&o)[8]) {
+    float A[8], B[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        o[k] = 0.0f;
+        A[k] = X[k * st];
+    }
+    int j = 0;
+    for (;;) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) B[k] = X[(8 * j + 8 + k) * st];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) o[k] = __fmaf_rn(w[8 * j + u], (k + u < 8) ? A[k + u] : B[k + u - 8], o[k]);
+        if (++j == nb) break;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) A[k] = X[(8 * j + 8 + k) * st];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) o[k] = __fmaf_rn(w[8 * j + u], (k + u < 8) ? B[k + u] : A[k + u - 8], o[k]);
+        if (++j == nb) break;
+    }
+}
+
+constexpr int ADJ_TM = 64;     // output rows per CTA of the column adjoint
+
+__host__ __device__ inline int adj_y_smem_floats(int tpad_max) { return (ADJ_TM + tpad_max + 8) * 32 + 2 * tpad_max; }
+
+// Column adjoint of level blockIdx.z: Y_i = B_y^T A_i (kernel w_i), Yd_i (dw_i),
+// a 32-column x 64-row tile per CTA, warp g on rows 8g .. 8g+7, lane = column.
 __global__ void __launch_bounds__(256) adj_y_kernel(const __grid_constant__ AdjParams p) {
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    extern __shared__ float ysm[];
     const int i = blockIdx.z;
-    if (x >= p.W || y >= p.H) return;
+    const int r = p.r[i], tpad = p.tpad[i], nb = tpad >> 3;
+    const int x0 = blockIdx.x * 32, m0 = blockIdx.y * ADJ_TM;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int rows = ADJ_TM + tpad + 8;
+    float* X = ysm;                  // rows x 32: A rows m0 - r + j, zero outside the frame
+    float* ws = ysm + rows * 32;     // tpad
+    float* wd = ws + tpad;           // tpad
     const size_t plane = (size_t)p.H * p.W;
-    const float* a = p.A + plane * i + x;
-    const int r = p.r[i];
-    p.Y[plane * i + (size_t)y * p.W + x] = adj1d(a, p.W, p.H, y, p.w + p.woff[i], r);
-    p.Yd[plane * i + (size_t)y * p.W + x] = adj1d(a, p.W, p.H, y, p.dw + p.woff[i], r);
+    const float* A = p.A + plane * i;
+    for (int t = threadIdx.x; t < tpad; t += blockDim.x) {
+        ws[t] = p.w[p.woff[i] + t];
+        wd[t] = p.dw[p.woff[i] + t];
+    }
+    const int x = x0 + lane;
+    for (int j = g; j < rows; j += 8) {
+        const int n = m0 - r + j;
+        X[j * 32 + lane] = (n >= 0 && n < p.H && x < p.W) ? A[(size_t)n * p.W + x] : 0.0f;
+    }
+    __syncthreads();
+    float o[8], od[8];
+    corr8x2(X + 8 * g * 32 + lane, 32, ws, wd, nb, o, od);
+    if (x >= p.W) return;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int m = m0 + 8 * g + k;
+        if (m >= p.H) break;
+        float y = o[k], yd = od[k];
+        if (m < r || m > p.H - 1 - r) {
+            y = adj1d(A + x, p.W, p.H, m, p.w + p.woff[i], r);
+            yd = adj1d(A + x, p.W, p.H, m, p.dw + p.woff[i], r);
+        }
+        p.Y[plane * i + (size_t)m * p.W + x] = y;
+        p.Yd[plane * i + (size_t)m * p.W + x] = yd;
+    }
+}
+
+constexpr int ADJ_XR = 32;     // output rows per CTA of the row adjoint (4 warps x 8)
+
+__host__ __device__ inline int adj_x_stride_y(int tpad_max) { return (32 + tpad_max + 8) | 1; }
+__host__ __device__ inline int adj_x_stride_i(int R) { return (32 + 2 * R + 16) | 1; }
+__host__ __device__ inline int adj_x_smem_floats(int tpad_max, int R) {
+    return ADJ_XR * (adj_x_stride_y(tpad_max) + adj_x_stride_i(R)) + 2 * tpad_max;
 }
 
 // Row adjoint summed over levels into dloss/dI, and the kernel-shape part of
-// dloss/dsigma_i = <Y_i, B_x' I> + <Yd_i, B_x I>.
-__global__ void __launch_bounds__(256) adj_x_kernel(const __grid_constant__ AdjParams p) {
-    __shared__ double red[8][MAX_LEVELS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x = blockIdx.x * 32 + lane;
-    const int y = blockIdx.y * 8 + warp;
-    const bool ok = x < p.W && y < p.H;
+// dloss/dsigma_i = <Y_i, B_x' I> + <Yd_i, B_x I>.  A CTA covers 32 columns x 32
+// rows; lane (rho, g) of warp q owns row 8q + rho, columns 8g .. 8g+7.
+__global__ void __launch_bounds__(128) adj_x_kernel(const __grid_constant__ AdjParams p, int tpad_max) {
+    extern __shared__ float xsm[];
+    __shared__ double red[4][MAX_LEVELS];
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int rho = lane >> 2, g4 = lane & 3;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * ADJ_XR;
+    const int row = 8 * q + rho;                 // 0 .. 31
+    const int y = y0 + row;
+    const int SY = adj_x_stride_y(tpad_max), SI = adj_x_stride_i(p.R);
+    float* Yt = xsm;                              // ADJ_XR x SY: Y_i rows, columns x0 - r + c, zero outside
+    float* It = Yt + ADJ_XR * SY;                 // ADJ_XR x SI: image rows, columns x0 - R + c, reflected
+    float* ws = It + ADJ_XR * SI;                 // tpad_max
+    float* wd = ws + tpad_max;                    // tpad_max
     const size_t plane = (size_t)p.H * p.W;
-    float g = 0.0f;
+    const int R = p.R;
+    for (int e = threadIdx.x; e < ADJ_XR * SI; e += blockDim.x) {
+        const int rr = e / SI, c = e - rr * SI;
+        const int yy = min(y0 + rr, p.H - 1);
+        It[e] = c < 32 + 2 * R + 16 ? __ldg(p.img + (size_t)yy * p.pitch + refl_i(x0 - R + c, p.W)) : 0.0f;
+    }
+    float gsum[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) gsum[k] = 0.0f;
     for (int i = 0; i < p.K; ++i) {
+        const int r = p.r[i], tpad = p.tpad[i], nb = tpad >> 3;
+        const float* Yi = p.Y + plane * i;
+        const float* Ydi = p.Yd + plane * i;
+        __syncthreads();
+        for (int t = threadIdx.x; t < tpad; t += blockDim.x) {
+            ws[t] = p.w[p.woff[i] + t];
+            wd[t] = p.dw[p.woff[i] + t];
+        }
+        const int wt = 32 + tpad + 8;
+        for (int e = threadIdx.x; e < ADJ_XR * wt; e += blockDim.x) {
+            const int rr = e / wt, c = e - rr * wt;
+            const int yy = y0 + rr, xx = x0 - r + c;
+            Yt[rr * SY + c] = (yy < p.H && xx >= 0 && xx < p.W) ? Yi[(size_t)yy * p.W + xx] : 0.0f;
+        }
+        __syncthreads();
+        float z[8], hb[8], hd[8];
+        corr8(Yt + row * SY + 8 * g4, 1, ws, nb, z);
+        corr8x2(It + row * SI + (R - r) + 8 * g4, 1, ws, wd, nb, hb, hd);    // B_x I and B_x' I
         double dot = 0.0;
-        if (ok) {
-            const int r = p.r[i];
-            const float* w = p.w + p.woff[i];
-            const float* dw = p.dw + p.woff[i];
-            g += adj1d(p.Y + plane * i + (size_t)y * p.W, 1, p.W, x, w, r);
-            float hb = 0.0f, hd = 0.0f;
-            const float* row = p.img + (size_t)y * p.pitch;
-            for (int k = -r; k <= r; ++k) {
-                const float v = __ldg(row + refl_i(x + k, p.W));
-                hb = __fmaf_rn(__ldg(w + r + k), v, hb);
-                hd = __fmaf_rn(__ldg(dw + r + k), v, hd);
+        if (y < p.H) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int x = x0 + 8 * g4 + k;
+                if (x >= p.W) break;
+                float zk = z[k];
+                if (x < r || x > p.W - 1 - r) zk = adj1d(Yi + (size_t)y * p.W, 1, p.W, x, p.w + p.woff[i], r);
+                gsum[k] += zk;
+                const size_t o = (size_t)y * p.W + x;
+                dot += (double)Yi[o] * (double)hd[k] + (double)Ydi[o] * (double)hb[k];
             }
-            const size_t o = plane * i + (size_t)y * p.W + x;
-            dot = (double)p.Y[o] * (double)hd + (double)p.Yd[o] * (double)hb;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        if (lane == 0) red[warp][i] = dot;
+        if (lane == 0) red[q][i] = dot;
     }
-    if (ok) p.gimg[(size_t)y * p.W + x] = g;
+    if (y < p.H) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int x = x0 + 8 * g4 + k;
+            if (x < p.W) p.gimg[(size_t)y * p.W + x] = gsum[k];
+        }
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < p.K; i += blockDim.x) {
         double s = 0.0;
-        for (int q = 0; q < 8; ++q) s += red[q][i];
+        for (int w = 0; w < 4; ++w) s += red[w][i];
         if (s != 0.0) atomicAdd(&p.dw_acc[i], s);
     }
 }
@@ -427,16 +578,20 @@ int soft_backward(dog_handle* h, const float* img, int H, int W, int pitch, cons
     a.K = K;
     a.w = ws->w;
     a.dw = ws->dw;
+    int tpad_max = 8;
     for (int i = 0; i < K; ++i) {
         a.r[i] = b.lv[i].r;
+        a.tpad[i] = b.lv[i].tpad;
         a.woff[i] = b.lv[i].woff;
+        tpad_max = std::max(tpad_max, b.lv[i].tpad);
     }
+    a.R = b.R;
     a.dw_acc = ws->acc + 2 * P;
-    dim3 gy((W + 31) / 32, (H + 7) / 8, K);
-    adj_y_kernel<<<gy, 256, 0, s>>>(a);
+    dim3 gy((W + 31) / 32, (H + ADJ_TM - 1) / ADJ_TM, K);
+    adj_y_kernel<<<gy, 256, sizeof(float) * adj_y_smem_floats(tpad_max), s>>>(a);
     SOFT_CUDA(cudaGetLastError());
-    dim3 gx((W + 31) / 32, (H + 7) / 8);
-    adj_x_kernel<<<gx, 256, 0, s>>>(a);
+    dim3 gx((W + 31) / 32, (H + ADJ_XR - 1) / ADJ_XR);
+    adj_x_kernel<<<gx, 128, sizeof(float) * adj_x_smem_floats(tpad_max, b.R), s>>>(a, tpad_max);
     SOFT_CUDA(cudaGetLastError());
     FinParams f{};
     f.sig = sig;
