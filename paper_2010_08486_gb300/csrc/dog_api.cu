@@ -205,8 +205,10 @@ static void assign_levels(dog_handle* h) {
         int best = 0;
         for (int w = 1; w < NWARPS; ++w)
             if (load[w] < load[best]) best = w;
-        // two passes of tpad/8 blocks (~80 issue slots each) plus per-level set-up
-        load[best] += 2 * (h->base.lv[i].tpad / 8) * 80 + 60;
+        // per level: two passes of tpad/8 tap blocks plus a fixed cost (set-up,
+        // pipeline fill and drain of both passes) of about 1.7 tap blocks of
+        // both passes (clock64 phase timers)
+        load[best] += 10 * (h->base.lv[i].tpad / 8) + 17;
         h->base.warp_lev[best][h->base.warp_nlev[best]++] = (unsigned char)i;
     }
 }
@@ -700,7 +702,8 @@ int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t m
     h->last = s;
     const int band = (h->band > 0) ? h->band : 0;
     // per-frame descriptors, candidate/output offsets and the tile prefix sum
-    DOG_CUDA(launch_batch_prep(d_frames, n, band, h->cand_cap, h->d_desc, h->d_cand_off, h->d_out_off,
+    const int grid = h->num_sms * h->ctas_per_sm;
+    DOG_CUDA(launch_batch_prep(d_frames, n, band, grid, h->cand_cap, h->d_desc, h->d_cand_off, h->d_out_off,
                                h->d_hw, h->d_ntiles, s));
     // fixed slots: the persistent kernel's work and completion counters are
     // zero between launches (the last CTA resets them), whatever n was
@@ -724,7 +727,6 @@ int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t m
     p.pend_cap = h->bpend_cap;
     p.pend_count = pend_count;
     p.ntiles_dev = h->d_ntiles;
-    const int grid = h->num_sms * h->ctas_per_sm;
     DOG_CUDA(timed_fused(h, p, grid, s));
     ResolveParams r = resolve_params(h, p);
     r.frames = h->d_desc;

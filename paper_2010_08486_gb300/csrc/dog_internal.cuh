@@ -56,6 +56,7 @@ struct FrameDesc {
     int32_t h, w, pitch, dtype;
     int64_t blob_off;
     int32_t n_strips, n_bands;
+    int32_t band, pad_;   // rows per band
     int64_t tile_begin;   // prefix sum of n_strips * n_bands over earlier frames
 };
 
@@ -140,8 +141,8 @@ struct ResolveParams {
 // ---- launchers (defined in the .cu files) -----------------------------------
 cudaError_t launch_fused(const FusedParams& p, int grid, cudaStream_t s);
 cudaError_t launch_resolve(const ResolveParams& p, int max_pending, cudaStream_t s);
-cudaError_t launch_batch_prep(const dog_frame* frames, int n, int band, int blob_cap, FrameDesc* desc,
-                              long long* cand_off, long long* out_off, int* hw, long long* ntiles,
+cudaError_t launch_batch_prep(const dog_frame* frames, int n, int band, int tail_tiles, int blob_cap,
+                              FrameDesc* desc, long long* cand_off, long long* out_off, int* hw, long long* ntiles,
                               cudaStream_t s);
 
 struct PruneParams {
