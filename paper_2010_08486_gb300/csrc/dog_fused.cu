@@ -324,6 +324,51 @@ __device__ __forceinline__ unsigned test_planes(const float* colp, const float* 
     return cmask;
 }
 
+// Plane loop of two adjacent test rows ya, yb = ya + 1 at once: their
+// 3x3 windows share rows ya and yb, so four L rows per plane serve both.  The
+// same operations as test_planes, row by row, so the masks are identical.
+// a_up / a_dn / b_up / b_dn: rows ya-1 / yb / ya / yb+1 lie inside the frame.
+template <int PB, bool FULL, bool EDGE>
+__device__ __forceinline__ void test_planes2(const float* colp, const float* cs, int P, int s0, int s1, int s2,
+                                             int s3, bool a_up, bool a_dn, bool b_up, bool b_dn, bool col_ok,
+                                             float thr, unsigned& cma, unsigned& cmb) {
+    const float NEG = -INFINITY;
+    float m2a = NEG, m1a = NEG, d1a = NEG, m2b = NEG, m1b = NEG, d1b = NEG;
+    unsigned ca = 0u, cb = 0u;
+    float L0 = colp[s0 * TX], L1 = colp[s1 * TX], L2 = colp[s2 * TX], L3 = colp[s3 * TX];
+#pragma unroll
+    for (int l = 0; l < PB; ++l) {
+        const bool on = FULL || l < P;
+        const float* pl = colp + (on ? l + 1 : P) * DSLOTS * TX;
+        const float n0 = pl[s0 * TX], n1 = pl[s1 * TX], n2 = pl[s2 * TX], n3 = pl[s3 * TX];
+        const float c = cs[l];
+        const float e0 = __fsub_rn(L0, n0), e1 = __fsub_rn(L1, n1), e2 = __fsub_rn(L2, n2), e3 = __fsub_rn(L3, n3);
+        L0 = n0; L1 = n1; L2 = n2; L3 = n3;
+        const float da = __fmul_rn(c, e1), db = __fmul_rn(c, e2);
+        const float mid = fmaxf(e1, e2);
+        const float va = EDGE ? fmaxf(a_up ? e0 : NEG, a_dn ? mid : e1) : fmaxf(e0, mid);
+        const float vb = EDGE ? fmaxf(b_up ? mid : e2, b_dn ? e3 : NEG) : fmaxf(mid, e3);
+        const bool live = EDGE ? (on && col_ok) : on;
+        const float ma = live ? __fmul_rn(c, va) : NEG;
+        const float mb = live ? __fmul_rn(c, vb) : NEG;
+        const float la = __shfl_up_sync(0xffffffffu, ma, 1), ra = __shfl_down_sync(0xffffffffu, ma, 1);
+        const float lb = __shfl_up_sync(0xffffffffu, mb, 1), rb = __shfl_down_sync(0xffffffffu, mb, 1);
+        const float m0a = fmaxf(ma, fmaxf(la, ra)), m0b = fmaxf(mb, fmaxf(lb, rb));
+        if (l >= 1) {
+            const bool okl = FULL || l - 1 < P;
+            ca |= (d1a >= fmaxf(m0a, fmaxf(m2a, m1a)) && d1a > thr && okl) ? (1u << (l - 1)) : 0u;
+            cb |= (d1b >= fmaxf(m0b, fmaxf(m2b, m1b)) && d1b > thr && okl) ? (1u << (l - 1)) : 0u;
+        }
+        m2a = m1a; m1a = m0a; d1a = da;
+        m2b = m1b; m1b = m0b; d1b = db;
+    }
+    const bool okl = FULL || PB - 1 < P;
+    ca |= (d1a >= fmaxf(m2a, m1a) && d1a > thr && okl) ? (1u << (PB - 1)) : 0u;
+    cb |= (d1b >= fmaxf(m2b, m1b) && d1b > thr && okl) ? (1u << (PB - 1)) : 0u;
+    cma = ca;
+    cmb = cb;
+}
+
 // D_l(y, x) of the test row (slot sc), recomputed for a candidate with the
 // operations of the plane loop.
 __device__ __forceinline__ float d_at(const float* colp, const float* cs, int l, int sc) {
@@ -359,6 +404,21 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
     for (int b = 0; b < nblk; ++b) {
         const int yb = yb0 + MB * b;
         bar_sync(BAR_FULL + (b & 1), NTHREADS);
+        // two rows per consumer warp: both masks from one plane loop
+        unsigned cm2a = 0u, cm2b = 0u;
+        if (MB / NCONS == 2 && mode != MODE_DUMP) {
+            const int wa = cw * 2;
+            const int ya = yb - 1 + wa;
+            const int s0 = (MB * b + wa) % DSLOTS, s1 = (MB * b + wa + 1) % DSLOTS;
+            const int s2 = (MB * b + wa + 2) % DSLOTS, s3 = (MB * b + wa + 3) % DSLOTS;
+            const bool a_up = ya - 1 >= 0, a_dn = ya + 1 < tc.H, b_up = ya >= 0, b_dn = ya + 2 < tc.H;
+            if (a_up && b_dn && tc.x0 + TX <= tc.W)
+                test_planes2<PB, FULL, false>(colp, ss.c, P, s0, s1, s2, s3, a_up, a_dn, b_up, b_dn, col_ok, thr,
+                                              cm2a, cm2b);
+            else
+                test_planes2<PB, FULL, true>(colp, ss.c, P, s0, s1, s2, s3, a_up, a_dn, b_up, b_dn, col_ok, thr,
+                                             cm2a, cm2b);
+        }
 #pragma unroll 1
         for (int q = 0; q < MB / NCONS; ++q) {
             const int w = cw * (MB / NCONS) + q;
@@ -379,7 +439,9 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                 continue;
             }
             unsigned cmask;
-            if (ym_ok && yp_ok && tc.x0 + TX <= tc.W)
+            if (MB / NCONS == 2)
+                cmask = q == 0 ? cm2a : cm2b;
+            else if (ym_ok && yp_ok && tc.x0 + TX <= tc.W)
                 cmask = test_planes<PB, FULL, false>(colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok, thr);
             else
                 cmask = test_planes<PB, FULL, true>(colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok, thr);

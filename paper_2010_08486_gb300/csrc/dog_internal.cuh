@@ -16,7 +16,7 @@ namespace dogk {
 constexpr int TX = 32;
 constexpr int MB = 8;
 constexpr int NWARPS = 8;                       // producer (blur) warps
-constexpr int NCONS = 8;                        // consumer (DoG + test) warps
+constexpr int NCONS = 4;                        // consumer (DoG + test) warps, two rows each
 constexpr int NPROD_T = NWARPS * 32;
 constexpr int NTHREADS = (NWARPS + NCONS) * 32;
 constexpr int RING_STRIDE = 32;    // floats per ring row (bank swizzle on row parity)
