@@ -460,7 +460,7 @@ def run_ours(a):
                              props.multi_processor_count, sm_max)},
             "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
                     "bytes_per_px": 2, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
-            "gpu_launches": 5 * a.steps,
+            "gpu_launches": 4 * a.steps,   # per step: batch prep, fused detection, strip-edge resolve, pruning + histogram
             "blobs_per_frame": n_blobs / B}
     clk_s = clk.summary()
     if clk_s:

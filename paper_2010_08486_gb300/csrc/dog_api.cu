@@ -655,9 +655,28 @@ int dog_detect(dog_t* h, const void* d_img, int32_t dtype, int32_t H, int32_t W,
     if (!h || !d_blobs || !d_count || cap < 0) return DOG_ERR_INVALID;
     int st = dog_candidates(h, d_img, dtype, H, W, pitch, h->d_cand, h->cand_cap, h->d_counts + 0, stream);
     if (st != DOG_OK) return st;
-    st = dog_prune(h, h->d_cand, h->d_counts + 0, h->cand_cap, H, W, d_blobs, cap, d_count, stream);
-    if (st != DOG_OK) return st;
-    if (d_hist) return dog_volume_hist(h, d_blobs, d_count, cap, d_hist, d_hist_vol, stream);
+    // pruning, with the histogram of the pruned blobs computed by the same
+    // kernel (one launch fewer on the single-frame latency path)
+    cudaStream_t s = (cudaStream_t)stream;
+    PruneParams q = prune_params(h);
+    q.cand = h->d_cand;
+    q.cand_count = h->d_counts + 0;
+    q.cap_in = h->cand_cap;
+    q.n_frames = 1;
+    q.H = H;
+    q.W = W;
+    q.state = h->d_state;
+    q.target = h->d_target;
+    q.order = h->d_order;
+    q.out = d_blobs;
+    q.cap_out = cap;
+    q.out_count = d_count;
+    if (d_hist) {
+        q.hist = hist_params(h);
+        q.hist.hist = d_hist;
+        q.hist.vol = d_hist_vol;
+    }
+    DOG_CUDA(launch_prune(q, s));
     return DOG_OK;
 }
 
@@ -750,20 +769,12 @@ int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t m
     q.cap_out = h->cand_cap;
     q.out_off = h->d_out_off;
     q.out_count = d_counts;
-    DOG_CUDA(launch_prune(q, s));
-    if (d_hists) {
-        const int nb = hist_bins(h);
-        DOG_CUDA(cudaMemsetAsync(d_hists, 0, sizeof(uint32_t) * (size_t)nb * n, s));
-        HistParams hp = hist_params(h);
-        hp.blobs = d_blobs;
-        hp.count = d_counts;
-        hp.cap = h->cand_cap;
-        hp.off = h->d_out_off;
-        hp.n_frames = n;
-        hp.hist = d_hists;
-        hp.vol = nullptr;
-        DOG_CUDA(launch_hist(hp, s));
+    if (d_hists) {   // each frame's histogram from its pruning CTA
+        q.hist = hist_params(h);
+        q.hist.hist = d_hists;
+        q.hist.vol = nullptr;
     }
+    DOG_CUDA(launch_prune(q, s));
     return DOG_OK;
 }
 

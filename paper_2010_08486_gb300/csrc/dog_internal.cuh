@@ -145,6 +145,22 @@ cudaError_t launch_batch_prep(const dog_frame* frames, int n, int band, int tail
                               FrameDesc* desc, long long* cand_off, long long* out_off, int* hw, long long* ntiles,
                               cudaStream_t s);
 
+struct HistParams {
+    const dog_blob* blobs;
+    const int* count;        // per frame
+    int cap;
+    const long long* off;    // per frame offset (nullptr: 0)
+    int n_frames;
+    int P, nbins, mode;      // mode: DOG_HIST_LOGV / DOG_HIST_LADDER
+    const float* sig_f;      // P plane sigmas rounded to float (on-ladder test)
+    const int* level_bin;    // P: bin of an on-ladder blob
+    const double* log_sig;   // P: ln sigma of each plane (double)
+    double log_lo, log_hi;   // ln sigma of the first / last DoG plane
+    unsigned* hist;          // n_frames x nbins_out
+    double* vol;             // n_frames x nbins_out or nullptr
+};
+cudaError_t launch_hist(const HistParams& p, cudaStream_t s);
+
 struct PruneParams {
     const dog_blob* cand;
     const int* cand_count;   // per frame
@@ -167,23 +183,12 @@ struct PruneParams {
     int* out_count;          // per frame
     int* status;
     int max_rounds;
+    // optional: the volume histogram of each frame's pruned blobs, computed by
+    // the same CTA after compaction (hist.hist non-null; hist.off, .blobs,
+    // .count and .cap are not used: the kernel's own output is binned)
+    HistParams hist;
 };
 cudaError_t launch_prune(const PruneParams& p, cudaStream_t s);
 
-struct HistParams {
-    const dog_blob* blobs;
-    const int* count;        // per frame
-    int cap;
-    const long long* off;    // per frame offset (nullptr: 0)
-    int n_frames;
-    int P, nbins, mode;      // mode: DOG_HIST_LOGV / DOG_HIST_LADDER
-    const float* sig_f;      // P plane sigmas rounded to float (on-ladder test)
-    const int* level_bin;    // P: bin of an on-ladder blob
-    const double* log_sig;   // P: ln sigma of each plane (double)
-    double log_lo, log_hi;   // ln sigma of the first / last DoG plane
-    unsigned* hist;          // n_frames x nbins_out
-    double* vol;             // n_frames x nbins_out or nullptr
-};
-cudaError_t launch_hist(const HistParams& p, cudaStream_t s);
 
 }  // namespace dogk

@@ -24,6 +24,36 @@
 
 namespace dogk {
 
+// Histogram bin of one blob (Sec. 4): a blob whose stored sigma equals its
+// plane's single-precision sigma takes its plane's precomputed bin; another
+// sigma (a coalesced mean) is binned by log volume (LOGV) or by the nearest
+// ladder radius in log space (LADDER).
+__device__ __forceinline__ int hist_bin(const dog_blob& b, const HistParams& p) {
+    const int l = min(max(b.level, 0), p.P - 1);
+    if (b.sigma == p.sig_f[l]) return p.level_bin[l];
+    if (p.mode == DOG_HIST_LADDER) {
+        const double ls = log((double)b.sigma);
+        int best = 0;
+        double bd = fabs(ls - p.log_sig[0]);
+        for (int q = 1; q < p.P; ++q) {
+            const double d = fabs(ls - p.log_sig[q]);
+            if (d < bd) { bd = d; best = q; }
+        }
+        return best;
+    }
+    const double span = p.log_hi - p.log_lo;
+    const double t = (p.P >= 2 && span > 0.0) ? (log((double)b.sigma) - p.log_lo) / span : 0.0;
+    double fb = floor((double)p.nbins * t);
+    fb = fmin(fmax(fb, 0.0), (double)(p.nbins - 1));
+    return (int)fb;
+}
+
+__device__ __forceinline__ double blob_volume(float sigma) {
+    const double r = 1.4142135623730951 * (double)sigma;
+    return 4.0 / 3.0 * 3.141592653589793 * r * r * r;
+}
+
+
 constexpr int PRUNE_THREADS = 1024;
 constexpr int NBUCKET = 4096;
 enum { ST_UND = 0, ST_IN = 1, ST_OUT = 2 };
@@ -59,6 +89,31 @@ __device__ __forceinline__ int neighbour_buckets(int cx, int cy, unsigned* bk) {
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) bk[nb++] = bucket_of(cx + dx, cy + dy);
     return nb;
+}
+
+// Volume histogram of one frame's pruned blobs (out[0 .. out_count[f])),
+// written whole by the frame's CTA (no other CTA touches it).
+__device__ void frame_hist(const PruneParams& p, PruneSmem& s, const dog_blob* out, int f) {
+    const HistParams& hp = p.hist;
+    const int tid = threadIdx.x;
+    const int nbo = (hp.mode == DOG_HIST_LADDER) ? hp.P : hp.nbins;
+    unsigned* hc = reinterpret_cast<unsigned*>(s.bcount);
+    double* hv = reinterpret_cast<double*>(s.boff);
+    __syncthreads();
+    for (int q = tid; q < nbo; q += PRUNE_THREADS) { hc[q] = 0u; hv[q] = 0.0; }
+    __syncthreads();
+    const int nout = min(p.out_count[f], p.cap_out);
+    for (int i = tid; i < nout; i += PRUNE_THREADS) {
+        const dog_blob b = out[i];
+        const int bin = hist_bin(b, hp);
+        atomicAdd(&hc[bin], 1u);
+        if (hp.vol) atomicAdd(&hv[bin], blob_volume(b.sigma));
+    }
+    __syncthreads();
+    for (int q = tid; q < nbo; q += PRUNE_THREADS) {
+        hp.hist[(size_t)f * nbo + q] = hc[q];
+        if (hp.vol) hp.vol[(size_t)f * nbo + q] = hv[q];
+    }
 }
 
 // Frames with at most PRUNE_SMEM_CAND candidates run every pass on
@@ -99,6 +154,7 @@ __global__ void __launch_bounds__(PRUNE_THREADS) dog_prune_kernel(const __grid_c
             p.out_count[f] = n;
             if (n > p.cap_out) atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
         }
+        if (p.hist.hist) frame_hist(p, s, out, f);
         return;
     }
 
@@ -255,6 +311,8 @@ __global__ void __launch_bounds__(PRUNE_THREADS) dog_prune_kernel(const __grid_c
         if (idx < p.cap_out) out[idx] = o;
         else atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
     }
+    // 5. optional: this frame's volume histogram
+    if (p.hist.hist) frame_hist(p, s, out, f);
 }
 
 static bool g_prune_attr[64];
@@ -286,31 +344,9 @@ __global__ void __launch_bounds__(256) dog_hist_kernel(const __grid_constant__ H
     const int n = min(p.count[f], p.cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const dog_blob b = p.blobs[off + i];
-        const int l = min(max(b.level, 0), p.P - 1);
-        int bin;
-        if (b.sigma == p.sig_f[l]) {
-            bin = p.level_bin[l];
-        } else if (p.mode == DOG_HIST_LADDER) {
-            const double ls = log((double)b.sigma);
-            int best = 0;
-            double bd = fabs(ls - p.log_sig[0]);
-            for (int q = 1; q < p.P; ++q) {
-                const double d = fabs(ls - p.log_sig[q]);
-                if (d < bd) { bd = d; best = q; }
-            }
-            bin = best;
-        } else {
-            const double span = p.log_hi - p.log_lo;
-            const double t = (p.P >= 2 && span > 0.0) ? (log((double)b.sigma) - p.log_lo) / span : 0.0;
-            double fb = floor((double)p.nbins * t);
-            fb = fmin(fmax(fb, 0.0), (double)(p.nbins - 1));
-            bin = (int)fb;
-        }
+        const int bin = hist_bin(b, p);
         atomicAdd(&hc[bin], 1u);
-        if (p.vol) {
-            const double r = 1.4142135623730951 * (double)b.sigma;
-            atomicAdd(&hv[bin], 4.0 / 3.0 * 3.141592653589793 * r * r * r);
-        }
+        if (p.vol) atomicAdd(&hv[bin], blob_volume(b.sigma));
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nbo; q += blockDim.x) {
