@@ -125,3 +125,32 @@ def test_autotuned_tiling_keeps_results(frames, tmp_path):
     assert sorted(zip(l.tolist(), y.tolist(), x.tolist(), s.tolist(), r.tolist())) == want[5][0]
     assert r1.band % 8 == 0
     assert det.status() == 0
+
+
+def test_bench_launch_configuration_matches_per_frame_and_oracle_histogram():
+    """The benchmark's launch: 96 uint16 1024x1024 frames in one persistent
+    launch (the last round of tiles cut into finer bands).  Sampled frames give
+    the blobs of the single-frame path, and histograms equal to the oracle's
+    histogram of those blobs."""
+    import oracle
+    from tests import parity
+    libbuild.build()
+    distinct = [synth.plif_frame_u16(synth.PLIF_SEED_BASE + k) for k in range(12)]
+    B = 96
+    frames = torch.from_numpy(np.stack([distinct[f % 12].view(np.int16) for f in range(B)])).cuda()
+    cfg = dog.plif_config(blob_cap=16384)
+    det = dog.Detector(cfg)
+    fl = [frames[f] for f in range(B)]
+    out, counts, hists = det.detect_batched(fl)
+    torch.cuda.synchronize()
+    assert det.status() == 0
+    got = unpack(det, out, counts, hists, B)
+    p = parity.oracle_params(cfg)
+    for f in (0, 47, 95):
+        blobs, hist, _ = det.detect(fl[f])
+        torch.cuda.synchronize()
+        x, y, l, s, r = blobs.to_numpy()
+        assert got[f][0] == sorted(zip(l.tolist(), y.tolist(), x.tolist(), s.tolist(), r.tolist()))
+        np.testing.assert_array_equal(got[f][1], hist.cpu().numpy())
+        want_counts, _ = oracle.hist(parity.blobs_to_oracle(x, y, l, s, r), p)
+        np.testing.assert_array_equal(got[f][1], want_counts.astype(np.int32))
