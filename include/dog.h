@@ -188,7 +188,7 @@ int dog_prune_noalloc(const dog_blob* d_cand, const int32_t* d_count, int32_t ca
                       const double* h_sigmas, int32_t n_planes, double overlap, int32_t mode,
                       dog_blob* d_out, int32_t cap_out, int32_t* d_nout, void* stream);
 
-/* Blob-volume histogram (Sec. 4, Sec. 4.1 "Blobs are then histogrammed").
+/* Blob-volume histogram (Sec. 4, Sec. 4.1: the pruned blobs are binned by volume).
  * d_hist: uint32 counts (nbins, or K-1 in LADDER mode), overwritten.
  * d_hist_vol: optional (NULL ok) double sum of V per bin, overwritten.
  * A blob whose stored sigma equals its plane's sigma (as float) is binned by

@@ -373,7 +373,7 @@ int ora_bin(float sigma_f32, int level, const double* sig_ladder, int K, int geo
     return b;
 }
 
-/* Sec. 4 "histogramming to produce a volume distribution": counts per bin and
+/* Sec. 4: the distribution of blob volumes as a histogram: counts per bin and
  * the summed volume per bin (volume from the stored sigma). */
 void ora_hist(int n, const float* sigma_f32, const int32_t* level, const double* sig_ladder,
               int K, int geom, int nbins, int mode, uint32_t* counts, double* vol) {
