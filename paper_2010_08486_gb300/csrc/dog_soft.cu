@@ -49,12 +49,14 @@ struct SoftWS {
     float* Y = nullptr;       // K x H x W
     float* Yd = nullptr;      // K x H x W
     double* acc = nullptr;    // dc (P), dt (P), dw (K)
+    float* last_sig = nullptr;   // the sigmas the tables were last built from (NaN: none)
 };
 
 void soft_free(dog_handle* h) {
     SoftWS* ws = static_cast<SoftWS*>(handle_soft_ws(h));
     if (!ws) return;
-    void* ptrs[] = {ws->w, ws->dw, ws->c, ws->kappa, ws->dkappa, ws->pend, ws->counts, ws->A, ws->Y, ws->Yd, ws->acc};
+    void* ptrs[] = {ws->w, ws->dw, ws->c, ws->kappa, ws->dkappa, ws->pend, ws->counts, ws->A, ws->Y, ws->Yd, ws->acc,
+                    ws->last_sig};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete ws;
@@ -85,6 +87,8 @@ static int soft_ws(dog_handle* h, int H, int W, SoftWS** out) {
     ok(cudaMalloc(&ws->Y, sizeof(float) * plane * K));
     ok(cudaMalloc(&ws->Yd, sizeof(float) * plane * K));
     ok(cudaMalloc(&ws->acc, sizeof(double) * (2 * P + K)));
+    ok(cudaMalloc(&ws->last_sig, sizeof(float) * K));
+    if (e == cudaSuccess) ok(cudaMemset(ws->last_sig, 0xff, sizeof(float) * K));   // NaN: tables not built
     if (e != cudaSuccess) {
         soft_free(h);
         return e == cudaErrorMemoryAllocation ? DOG_ERR_NOMEM : DOG_ERR_CUDA;
@@ -109,11 +113,19 @@ struct SoftPrep {
     float* c;
     float* kappa;
     float* dkappa;
+    float* last_sig;
 };
 
-__global__ void __launch_bounds__(256) soft_prep_kernel(const __grid_constant__ SoftPrep p) {
+// Tap, coefficient and bin-weight tables of the device sigmas.  Skipped when
+// the sigmas equal those the tables were last built from (a batch of frames
+// at one ladder builds them once); last_sig is NaN after allocation.
+constexpr int PREP_THREADS = 512;
+__global__ void __launch_bounds__(PREP_THREADS) soft_prep_kernel(const __grid_constant__ SoftPrep p) {
+    bool changed = false;
+    for (int i = threadIdx.x; i < p.K; i += blockDim.x) changed |= !(p.sig[i] == p.last_sig[i]);
+    if (!__syncthreads_or(changed)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < p.K; i += 8) {
+    for (int i = warp; i < p.K; i += PREP_THREADS / 32) {
         const double s = (double)p.sig[i];
         const int r = p.r[i];
         double z = 0.0, m2 = 0.0;
@@ -158,6 +170,7 @@ __global__ void __launch_bounds__(256) soft_prep_kernel(const __grid_constant__ 
             p.dkappa[l * p.nbins + b] = (a < 1.0 && !clamped) ? (float)(-(double)p.nbins * sg) : 0.0f;
         }
     }
+    for (int i = threadIdx.x; i < p.K; i += blockDim.x) p.last_sig[i] = p.sig[i];
 }
 
 static SoftPrep prep_params(dog_handle* h, SoftWS* ws, const float* sig) {
@@ -182,6 +195,7 @@ static SoftPrep prep_params(dog_handle* h, SoftWS* ws, const float* sig) {
     q.c = ws->c;
     q.kappa = ws->kappa;
     q.dkappa = ws->dkappa;
+    q.last_sig = ws->last_sig;
     return q;
 }
 
@@ -257,7 +271,7 @@ int soft_forward(dog_handle* h, const float* img, int H, int W, int pitch, const
     int st = soft_ws(h, H, W, &ws);
     if (st != DOG_OK) return st;
     SoftPrep q = prep_params(h, ws, sig);
-    soft_prep_kernel<<<1, 256, 0, s>>>(q);
+    soft_prep_kernel<<<1, PREP_THREADS, 0, s>>>(q);
     SOFT_CUDA(cudaGetLastError());
     SOFT_CUDA(cudaMemsetAsync(ws->counts, 0, sizeof(int) * 4, s));
     FusedParams p = soft_fused(h, ws, img, H, W, pitch, MODE_SOFT);
@@ -268,27 +282,34 @@ int soft_forward(dog_handle* h, const float* img, int H, int W, int pitch, const
 }
 
 // ---------------------------------------------------------------------------
-// 1-D adjoint of a reflect-boundary correlation with the symmetric full kernel
-// w[0..2r] (w[r + d] weighs offset d), evaluated at index m of a line of length N with stride `st`:
-// sum over the preimages q of m under the reflection that lie within r of the
-// line, of sum_n w[|q-n|] a[n].
-__device__ __forceinline__ float adj1d(const float* __restrict__ a, size_t st, int N, int m,
-                                       const float* __restrict__ w, int r) {
+// Reflected part of the 1-D adjoint of a reflect-boundary correlation with the
+// symmetric full kernel w[0..2r] (w[r + d] weighs offset d), at index m of a
+// line of length N with stride `st`.  The adjoint at m sums, over the
+// preimages q of m under the reflection that lie within r of the line,
+// sum_n w[|q-n|] a[n]; the zero-padded correlation gives the term q = m, and
+// this function the others (the reflected copies q = -1-m, 2N-1-m, ...).
+__device__ __forceinline__ float adj1d_mirror(const float* __restrict__ a, size_t st, int N, int m,
+                                              const float* __restrict__ w, int r) {
     float acc = 0.0f;
     const int per = 2 * N;
     const int fam[2] = {m, per - 1 - m};
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
         int q = fam[f];
-        // first q of this family >= -r
         const int k = (-r - q) > 0 ? ((-r - q) + per - 1) / per : -((q + r) / per);
         for (q = q + k * per; q <= N - 1 + r; q += per) {
+            if (q == m) continue;
             const int nlo = max(0, q - r), nhi = min(N - 1, q + r);
             for (int n = nlo; n <= nhi; ++n) acc = __fmaf_rn(__ldg(w + r + (q - n)), __ldg(a + (size_t)n * st), acc);
         }
     }
     return acc;
 }
+
+// Outputs of a line of length N that a reflected preimage reaches (those
+// within r of an end): count, and the j-th of them.
+__host__ __device__ inline int fold_count(int N, int r) { return N <= 2 * r ? N : 2 * r; }
+__host__ __device__ inline int fold_index(int N, int r, int j) { return (N <= 2 * r || j < r) ? j : N - 2 * r + j; }
 
 __device__ __forceinline__ int refl_i(int i, int n) {
     int p = 2 * n;
@@ -318,8 +339,9 @@ struct AdjParams {
 // correlation: out(m) = sum_{u < Tpad} k[u] X(m - r + u) over zero-padded taps.
 // Eight consecutive outputs per thread are accumulated against a two-window
 // register file (8 inputs per block of 8 taps), for two tap sets at once.
-// Outputs within r of an edge, where the reflect boundary folds the sums, take
-// the exact preimage gather (adj1d).
+// Outputs within r of an edge, where the reflect boundary folds the sums, get
+// the reflected preimages' part added afterwards by the fold kernels, one
+// thread per such output (adj1d_mirror).
 __device__ __forceinline__ void tap_block2(float (&o)[8], float (&od)[8], const float (&A)[8], const float (&B)[8],
                                            const float* __restrict__ w, const float* __restrict__ dw) {
 #pragma unroll
@@ -408,9 +430,17 @@ __global__ void __launch_bounds__(256) adj_y_kernel(const __grid_constant__ AdjP
         wd[t] = p.dw[p.woff[i] + t];
     }
     const int x = x0 + lane;
-    for (int j = g; j < rows; j += 8) {
-        const int n = m0 - r + j;
-        X[j * 32 + lane] = (n >= 0 && n < p.H && x < p.W) ? A[(size_t)n * p.W + x] : 0.0f;
+    // warp g stages rows g, g + 8, ...; eight loads in flight before the stores
+    for (int j0 = g; j0 < rows; j0 += 64) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = j0 + 8 * u, n = m0 - r + j;
+            v[u] = (j < rows && n >= 0 && n < p.H && x < p.W) ? A[(size_t)n * p.W + x] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (j0 + 8 * u < rows) X[(j0 + 8 * u) * 32 + lane] = v[u];
     }
     __syncthreads();
     float o[8], od[8];
@@ -420,14 +450,44 @@ __global__ void __launch_bounds__(256) adj_y_kernel(const __grid_constant__ AdjP
     for (int k = 0; k < 8; ++k) {
         const int m = m0 + 8 * g + k;
         if (m >= p.H) break;
-        float y = o[k], yd = od[k];
-        if (m < r || m > p.H - 1 - r) {
-            y = adj1d(A + x, p.W, p.H, m, p.w + p.woff[i], r);
-            yd = adj1d(A + x, p.W, p.H, m, p.dw + p.woff[i], r);
-        }
-        p.Y[plane * i + (size_t)m * p.W + x] = y;
-        p.Yd[plane * i + (size_t)m * p.W + x] = yd;
+        p.Y[plane * i + (size_t)m * p.W + x] = o[k];
+        p.Yd[plane * i + (size_t)m * p.W + x] = od[k];
     }
+}
+
+// Reflect fold of the column adjoint: rows within r_i of the top or bottom
+// edge (blockIdx.y-th of them) of level blockIdx.z, one thread per column.
+__global__ void __launch_bounds__(128) adj_y_fold_kernel(const __grid_constant__ AdjParams p) {
+    const int i = blockIdx.z, r = p.r[i];
+    const int j = blockIdx.y;
+    if (j >= fold_count(p.H, r)) return;
+    const int m = fold_index(p.H, r, j);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.W) return;
+    const size_t plane = (size_t)p.H * p.W;
+    const float* A = p.A + plane * i + x;
+    const size_t o = plane * i + (size_t)m * p.W + x;
+    p.Y[o] += adj1d_mirror(A, p.W, p.H, m, p.w + p.woff[i], r);
+    p.Yd[o] += adj1d_mirror(A, p.W, p.H, m, p.dw + p.woff[i], r);
+}
+
+// Reflect fold of the row adjoint: columns within R of the left or right edge
+// (blockIdx.x-th of them), one thread per row; sums the reflected preimages'
+// part over every level whose radius reaches the column.
+__global__ void __launch_bounds__(128) adj_x_fold_kernel(const __grid_constant__ AdjParams p) {
+    const int j = blockIdx.x;
+    if (j >= fold_count(p.W, p.R)) return;
+    const int x = fold_index(p.W, p.R, j);
+    const int y = blockIdx.y * blockDim.x + threadIdx.x;
+    if (y >= p.H) return;
+    const size_t plane = (size_t)p.H * p.W;
+    float v = 0.0f;
+    for (int i = 0; i < p.K; ++i) {
+        const int r = p.r[i];
+        if (x >= r && x <= p.W - 1 - r) continue;
+        v += adj1d_mirror(p.Y + plane * i + (size_t)y * p.W, 1, p.W, x, p.w + p.woff[i], r);
+    }
+    p.gimg[(size_t)y * p.W + x] += v;
 }
 
 constexpr int ADJ_XR = 32;     // output rows per CTA of the row adjoint (4 warps x 8)
@@ -456,10 +516,26 @@ __global__ void __launch_bounds__(128) adj_x_kernel(const __grid_constant__ AdjP
     float* wd = ws + tpad_max;                    // tpad_max
     const size_t plane = (size_t)p.H * p.W;
     const int R = p.R;
-    for (int e = threadIdx.x; e < ADJ_XR * SI; e += blockDim.x) {
-        const int rr = e / SI, c = e - rr * SI;
-        const int yy = min(y0 + rr, p.H - 1);
-        It[e] = c < 32 + 2 * R + 16 ? __ldg(p.img + (size_t)yy * p.pitch + refl_i(x0 - R + c, p.W)) : 0.0f;
+    // image rows y0 .. y0+31 (clamped), columns x0-R .. x0+R+47 (reflected);
+    // thread t stages columns t, t + 128 of every row
+    {
+        const int c0 = threadIdx.x, c1 = threadIdx.x + 128;
+        const int xr0 = refl_i(x0 - R + c0, p.W), xr1 = refl_i(x0 - R + c1, p.W);
+        const bool ok0 = c0 < 32 + 2 * R + 16, ok1 = c1 < 32 + 2 * R + 16;
+        for (int rr0 = 0; rr0 < ADJ_XR; rr0 += 8) {   // 16 loads in flight before the stores
+            float v0[8], v1[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float* src = p.img + (size_t)min(y0 + rr0 + u, p.H - 1) * p.pitch;
+                v0[u] = ok0 ? __ldg(src + xr0) : 0.0f;
+                v1[u] = ok1 ? __ldg(src + xr1) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (c0 < SI) It[(rr0 + u) * SI + c0] = v0[u];
+                if (c1 < SI) It[(rr0 + u) * SI + c1] = v1[u];
+            }
+        }
     }
     float gsum[8];
 #pragma unroll
@@ -474,28 +550,44 @@ __global__ void __launch_bounds__(128) adj_x_kernel(const __grid_constant__ AdjP
             wd[t] = p.dw[p.woff[i] + t];
         }
         const int wt = 32 + tpad + 8;
-        for (int e = threadIdx.x; e < ADJ_XR * wt; e += blockDim.x) {
-            const int rr = e / wt, c = e - rr * wt;
-            const int yy = y0 + rr, xx = x0 - r + c;
-            Yt[rr * SY + c] = (yy < p.H && xx >= 0 && xx < p.W) ? Yi[(size_t)yy * p.W + xx] : 0.0f;
+        {   // Y_i rows y0 .. y0+31, columns x0-r .. x0-r+wt-1 (zero outside the frame)
+            const int c0 = threadIdx.x, c1 = threadIdx.x + 128;
+            const int xx0 = x0 - r + c0, xx1 = x0 - r + c1;
+            const bool ok0 = c0 < wt && xx0 >= 0 && xx0 < p.W, ok1 = c1 < wt && xx1 >= 0 && xx1 < p.W;
+            for (int rr0 = 0; rr0 < ADJ_XR; rr0 += 8) {   // 16 loads in flight before the stores
+                float v0[8], v1[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int yy = y0 + rr0 + u;
+                    const float* src = Yi + (size_t)yy * p.W;
+                    v0[u] = (ok0 && yy < p.H) ? src[xx0] : 0.0f;
+                    v1[u] = (ok1 && yy < p.H) ? src[xx1] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (c0 < wt) Yt[(rr0 + u) * SY + c0] = v0[u];
+                    if (c1 < wt) Yt[(rr0 + u) * SY + c1] = v1[u];
+                }
+            }
         }
         __syncthreads();
         float z[8], hb[8], hd[8];
         corr8(Yt + row * SY + 8 * g4, 1, ws, nb, z);
         corr8x2(It + row * SI + (R - r) + 8 * g4, 1, ws, wd, nb, hb, hd);    // B_x I and B_x' I
-        double dot = 0.0;
+        // this thread's 16 products in FP32 (one rounding each, as the inputs
+        // are FP32), then the warp's sum in FP64 (the FP64 pipe is slow here)
+        float dotf = 0.0f;
         if (y < p.H) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int x = x0 + 8 * g4 + k;
                 if (x >= p.W) break;
-                float zk = z[k];
-                if (x < r || x > p.W - 1 - r) zk = adj1d(Yi + (size_t)y * p.W, 1, p.W, x, p.w + p.woff[i], r);
-                gsum[k] += zk;
-                const size_t o = (size_t)y * p.W + x;
-                dot += (double)Yi[o] * (double)hd[k] + (double)Ydi[o] * (double)hb[k];
+                gsum[k] += z[k];
+                const float yv = Yt[row * SY + r + 8 * g4 + k];   // Y_i(y, x)
+                dotf = __fmaf_rn(yv, hd[k], __fmaf_rn(Ydi[(size_t)y * p.W + x], hb[k], dotf));
             }
         }
+        double dot = (double)dotf;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
         if (lane == 0) red[q][i] = dot;
@@ -553,7 +645,7 @@ int soft_backward(dog_handle* h, const float* img, int H, int W, int pitch, cons
     int st = soft_ws(h, H, W, &ws);
     if (st != DOG_OK) return st;
     SoftPrep q = prep_params(h, ws, sig);
-    soft_prep_kernel<<<1, 256, 0, s>>>(q);
+    soft_prep_kernel<<<1, PREP_THREADS, 0, s>>>(q);
     SOFT_CUDA(cudaGetLastError());
     const FusedParams& b = handle_base(h);
     const int K = b.K, P = b.P;
@@ -590,8 +682,14 @@ int soft_backward(dog_handle* h, const float* img, int H, int W, int pitch, cons
     dim3 gy((W + 31) / 32, (H + ADJ_TM - 1) / ADJ_TM, K);
     adj_y_kernel<<<gy, 256, sizeof(float) * adj_y_smem_floats(tpad_max), s>>>(a);
     SOFT_CUDA(cudaGetLastError());
+    dim3 gyf((W + 127) / 128, fold_count(H, b.R), K);
+    adj_y_fold_kernel<<<gyf, 128, 0, s>>>(a);
+    SOFT_CUDA(cudaGetLastError());
     dim3 gx((W + 31) / 32, (H + ADJ_XR - 1) / ADJ_XR);
     adj_x_kernel<<<gx, 128, sizeof(float) * adj_x_smem_floats(tpad_max, b.R), s>>>(a, tpad_max);
+    SOFT_CUDA(cudaGetLastError());
+    dim3 gxf(fold_count(W, b.R), (H + 127) / 128);
+    adj_x_fold_kernel<<<gxf, 128, 0, s>>>(a);
     SOFT_CUDA(cudaGetLastError());
     FinParams f{};
     f.sig = sig;
