@@ -239,6 +239,32 @@ int dog_backward(dog_t* h, const float* d_img, int32_t img_h, int32_t img_w, int
                  const float* d_sigmas, const float* d_grad_hist, float* d_grad_img,
                  float* d_grad_sigmas, void* stream);
 
+/* One hard local maximum v of the soft histogram's forward pass, as the
+ * backward needs it (the mask is held constant): voxel (x, y, level l),
+ * q = s_v (1 - s_v) / soft_T, qe = q (L_l - L_{l+1})(v) and s = s_v, with
+ * s_v = sigmoid((D_v - threshold) / soft_T).  24 bytes. */
+typedef struct dog_soft_max {
+    int32_t x, y, level;
+    float q, qe, s;
+} dog_soft_max;
+
+/* dog_soft_hist that also records every maximum into d_max (device, up to
+ * cap entries, in no particular order); *d_count (device) receives their true
+ * number, so *d_count > cap means the list is incomplete (the status word is
+ * then DOG_ERR_CAPACITY and the list must not be passed to dog_backward_rec). */
+int dog_soft_hist_rec(dog_t* h, const float* d_img, int32_t img_h, int32_t img_w, int32_t pitch,
+                      const float* d_sigmas, float* d_soft_hist, dog_soft_max* d_max, int32_t cap,
+                      int32_t* d_count, void* stream);
+
+/* Backward of dog_soft_hist_rec from its list of maxima (same frame, same
+ * d_sigmas): the dloss/dL planes are scattered from the list and no blur level
+ * is recomputed; then the same adjoint blurs as dog_backward.  Outputs as in
+ * dog_backward.  An incomplete list (*d_count > cap) sets DOG_ERR_CAPACITY and
+ * uses the first cap entries. */
+int dog_backward_rec(dog_t* h, const float* d_img, int32_t img_h, int32_t img_w, int32_t pitch,
+                     const float* d_sigmas, const dog_soft_max* d_max, const int32_t* d_count, int32_t cap,
+                     const float* d_grad_hist, float* d_grad_img, float* d_grad_sigmas, void* stream);
+
 /* Debug/parity: write the DoG cube D (K-1 x img_h x img_w floats, row-major
  * planes) computed by the same fused kernel as dog_candidates. */
 int dog_debug_dog(dog_t* h, const void* d_img, int32_t dtype, int32_t img_h, int32_t img_w,

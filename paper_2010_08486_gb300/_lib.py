@@ -32,7 +32,7 @@ NOALLOC_MAX_CAND = 65536
 EXPORTS = (
     "dog_config_default", "dog_create", "dog_destroy", "dog_ladder", "dog_candidates", "dog_prune",
     "dog_prune_noalloc", "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_soft_hist",
-    "dog_backward", "dog_debug_dog", "dog_ring_hist_push", "dog_ring_hist_push_batched",
+    "dog_backward", "dog_soft_hist_rec", "dog_backward_rec", "dog_debug_dog", "dog_ring_hist_push", "dog_ring_hist_push_batched",
     "dog_profile_enable", "dog_profile_read",
     "dog_get_status", "dog_status_string",
 )
@@ -121,6 +121,8 @@ def load(path: str | None = None):
         lib.dog_set_tiling.argtypes = [vp, i32, i32]
         lib.dog_soft_hist.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp]
         lib.dog_backward.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
+        lib.dog_soft_hist_rec.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, i32, vp, vp]
+        lib.dog_backward_rec.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, i32, vp, vp, vp, vp]
         lib.dog_debug_dog.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp]
         lib.dog_ring_hist_push.argtypes = [vp, i32, vp, i32, vp, vp, vp]
         lib.dog_ring_hist_push_batched.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp, vp]

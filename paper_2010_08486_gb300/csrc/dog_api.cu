@@ -18,9 +18,12 @@ cudaError_t launch_ring_push_batched(const uint32_t* hists, const int32_t* ids, 
                                      uint32_t* rings, int window, uint32_t* sums, int32_t* heads, cudaStream_t s);
 // differentiable form (dog_soft.cu)
 int soft_forward(dog_handle* h, const float* img, int H, int W, int pitch, const float* sig, float* out,
-                 cudaStream_t s);
+                 dog_soft_max* rec, int rec_cap, int* rec_count, cudaStream_t s);
 int soft_backward(dog_handle* h, const float* img, int H, int W, int pitch, const float* sig,
                   const float* gH, float* gimg, float* gsig, cudaStream_t s);
+int soft_backward_rec(dog_handle* h, const float* img, int H, int W, int pitch, const float* sig,
+                      const dog_soft_max* rec, const int* rec_count, int rec_cap, const float* gH, float* gimg,
+                      float* gsig, cudaStream_t s);
 }  // namespace dogk
 
 using namespace dogk;
@@ -784,7 +787,28 @@ int dog_soft_hist(dog_t* h, const float* d_img, int32_t H, int32_t W, int32_t pi
     int st = check_frame(h, d_img, DOG_DTYPE_F32, H, W, pitch);
     if (st != DOG_OK) return st;
     h->last = (cudaStream_t)stream;
-    return soft_forward(h, d_img, H, W, pitch, d_sigmas, d_soft_hist, (cudaStream_t)stream);
+    return soft_forward(h, d_img, H, W, pitch, d_sigmas, d_soft_hist, nullptr, 0, nullptr, (cudaStream_t)stream);
+}
+
+int dog_soft_hist_rec(dog_t* h, const float* d_img, int32_t H, int32_t W, int32_t pitch, const float* d_sigmas,
+                      float* d_soft_hist, dog_soft_max* d_max, int32_t cap, int32_t* d_count, void* stream) {
+    if (!h || !d_sigmas || !d_soft_hist || !d_max || !d_count || cap < 1) return DOG_ERR_INVALID;
+    int st = check_frame(h, d_img, DOG_DTYPE_F32, H, W, pitch);
+    if (st != DOG_OK) return st;
+    h->last = (cudaStream_t)stream;
+    return soft_forward(h, d_img, H, W, pitch, d_sigmas, d_soft_hist, d_max, cap, d_count, (cudaStream_t)stream);
+}
+
+int dog_backward_rec(dog_t* h, const float* d_img, int32_t H, int32_t W, int32_t pitch, const float* d_sigmas,
+                     const dog_soft_max* d_max, const int32_t* d_count, int32_t cap, const float* d_grad_hist,
+                     float* d_grad_img, float* d_grad_sigmas, void* stream) {
+    if (!h || !d_sigmas || !d_max || !d_count || cap < 1 || !d_grad_hist || !d_grad_img || !d_grad_sigmas)
+        return DOG_ERR_INVALID;
+    int st = check_frame(h, d_img, DOG_DTYPE_F32, H, W, pitch);
+    if (st != DOG_OK) return st;
+    h->last = (cudaStream_t)stream;
+    return soft_backward_rec(h, d_img, H, W, pitch, d_sigmas, d_max, d_count, cap, d_grad_hist, d_grad_img,
+                             d_grad_sigmas, (cudaStream_t)stream);
 }
 
 int dog_backward(dog_t* h, const float* d_img, int32_t H, int32_t W, int32_t pitch, const float* d_sigmas,

@@ -494,13 +494,42 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                     }
                 }
             } else if (mode == MODE_SOFT) {
+                // optional record of the maxima for the backward: one slot
+                // reservation per row, as for candidates
+                int idx = 0;
+                if (p.rec != nullptr) {
+                    const int nmine = __popc(dmask);
+                    int incl = nmine;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += t;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, incl, 31);
+                    int base = 0;
+                    if (lane == 0 && total) base = atomicAdd(p.rec_count, total);
+                    idx = __shfl_sync(0xffffffffu, base, 0) + incl - nmine;
+                }
                 unsigned rest = dmask;
                 while (rest) {
                     const int l = __ffs(rest) - 1;
                     rest &= rest - 1;
-                    const float s = 1.0f / (1.0f + __expf(-(d_at(colp, ss.c, l, sc) - p.thr) * p.inv_T));
+                    const float e = __fsub_rn(colp[l * DSLOTS * TX + sc * TX], colp[(l + 1) * DSLOTS * TX + sc * TX]);
+                    const float d = __fmul_rn(ss.c[l], e);   // = d_at(colp, ss.c, l, sc)
+                    const float s = 1.0f / (1.0f + __expf(-(d - p.thr) * p.inv_T));
                     atomicAdd(&ss.soft[ss.kb[l][0]], s * ss.kw[l][0]);
                     atomicAdd(&ss.soft[ss.kb[l][1]], s * ss.kw[l][1]);
+                    if (p.rec != nullptr) {
+                        if (idx < p.rec_cap) {
+                            const float q = s * (1.0f - s) * p.inv_T;
+                            dog_soft_max m;
+                            m.x = gx; m.y = y; m.level = l; m.q = q; m.qe = q * e; m.s = s;
+                            p.rec[idx] = m;
+                        } else {
+                            atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
+                        }
+                        ++idx;
+                    }
                 }
             } else {
                 // backward prologue: dense dloss/dL rows A_l = c_l G_l - c_{l-1} G_{l-1}
@@ -855,6 +884,19 @@ __global__ void __launch_bounds__(RES_THREADS) dog_resolve_kernel(const __grid_c
                         for (int b = 0; b < p.nbins; ++b) {
                             const float k = p.kappa[l * p.nbins + b];
                             if (k != 0.0f) atomicAdd(&p.soft_out[b], s * k);
+                        }
+                        if (p.rec != nullptr) {
+                            const int idx = atomicAdd(p.rec_count, 1);
+                            if (idx < p.rec_cap) {
+                                const float q = s * (1.0f - s) * p.inv_T;
+                                dog_soft_max m;
+                                m.x = e.x; m.y = e.y; m.level = l; m.q = q;
+                                m.qe = q * (e.response / __ldg(p.c + l));
+                                m.s = s;
+                                p.rec[idx] = m;
+                            } else {
+                                atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
+                            }
                         }
                     } else {
                         float gk = 0.0f, gdk = 0.0f;

@@ -97,6 +97,9 @@ struct FusedParams {
     float* A;              // K x H x W dloss/dL planes (MODE_BWD)
     double* dc_acc;        // P: dloss/dc
     double* dt_acc;        // P: dloss/dt
+    dog_soft_max* rec;     // MODE_SOFT: maxima recorded for the backward (or nullptr)
+    int rec_cap;
+    int* rec_count;
     int* status;
     // shared-memory layout (floats)
     int in_off, in_rows, in_stride;
@@ -135,6 +138,9 @@ struct ResolveParams {
     float* A;
     double* dc_acc;
     double* dt_acc;
+    dog_soft_max* rec;
+    int rec_cap;
+    int* rec_count;
     int* status;
 };
 

@@ -254,6 +254,9 @@ static ResolveParams soft_resolve(dog_handle* h, const FusedParams& f) {
     r.A = f.A;
     r.dc_acc = f.dc_acc;
     r.dt_acc = f.dt_acc;
+    r.rec = f.rec;
+    r.rec_cap = f.rec_cap;
+    r.rec_count = f.rec_count;
     r.status = handle_status(h);
     (void)h;
     return r;
@@ -266,7 +269,7 @@ static ResolveParams soft_resolve(dog_handle* h, const FusedParams& f) {
     } while (0)
 
 int soft_forward(dog_handle* h, const float* img, int H, int W, int pitch, const float* sig, float* out,
-                 cudaStream_t s) {
+                 dog_soft_max* rec, int rec_cap, int* rec_count, cudaStream_t s) {
     SoftWS* ws = nullptr;
     int st = soft_ws(h, H, W, &ws);
     if (st != DOG_OK) return st;
@@ -276,6 +279,12 @@ int soft_forward(dog_handle* h, const float* img, int H, int W, int pitch, const
     SOFT_CUDA(cudaMemsetAsync(ws->counts, 0, sizeof(int) * 4, s));
     FusedParams p = soft_fused(h, ws, img, H, W, pitch, MODE_SOFT);
     p.soft_out = out;
+    if (rec != nullptr) {
+        SOFT_CUDA(cudaMemsetAsync(rec_count, 0, sizeof(int), s));
+        p.rec = rec;
+        p.rec_cap = rec_cap;
+        p.rec_count = rec_count;
+    }
     SOFT_CUDA(timed_fused(h, p, p.n_strips * p.n_bands, s));
     SOFT_CUDA(launch_resolve(soft_resolve(h, p), std::min(ws->pend_cap, 152 * 64), s));
     return DOG_OK;
@@ -639,6 +648,68 @@ __global__ void soft_finalize_kernel(const __grid_constant__ FinParams p) {
     p.gsig[i] += (float)g;
 }
 
+// dloss/dL planes from a recorded list of maxima: A_l += c_l G_v and
+// A_{l+1} -= c_l G_v for a maximum v in plane l, G_v = gk_l q_v with
+// gk_l = sum_b gH_b kappa_b(t_l); dloss/dc_l += gk_l qe_v, dloss/dt_l +=
+// s_v sum_b gH_b dkappa_b(t_l).  A must be zero beforehand.
+struct ScatterParams {
+    const dog_soft_max* rec;
+    const int* count;
+    int cap;
+    const float* gH;
+    const float* kappa;
+    const float* dkappa;
+    const float* c;
+    int P, nbins, H, W;
+    float* A;
+    double* dc_acc;
+    double* dt_acc;
+    int* status;
+};
+
+__global__ void __launch_bounds__(256) soft_scatter_kernel(const __grid_constant__ ScatterParams p) {
+    __shared__ float gk[MAX_LEVELS], gdk[MAX_LEVELS], cl[MAX_LEVELS], dc[MAX_LEVELS], dt[MAX_LEVELS];
+    for (int l = threadIdx.x; l < p.P; l += blockDim.x) {
+        float a = 0.0f, b = 0.0f;
+        for (int k = 0; k < p.nbins; ++k) {
+            a += p.gH[k] * p.kappa[l * p.nbins + k];
+            b += p.gH[k] * p.dkappa[l * p.nbins + k];
+        }
+        gk[l] = a;
+        gdk[l] = b;
+        cl[l] = p.c[l];
+        dc[l] = 0.0f;
+        dt[l] = 0.0f;
+    }
+    __syncthreads();
+    const int n = *p.count;
+    if (n > p.cap && blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
+    const int m = min(n, p.cap);
+    const size_t plane = (size_t)p.H * p.W;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const dog_soft_max v = p.rec[i];
+        const int l = v.level;
+        if (v.x < 0 || v.x >= p.W || v.y < 0 || v.y >= p.H || l < 0 || l >= p.P) {   // not this frame's record
+            atomicCAS(p.status, 0, (int)DOG_ERR_INVALID);
+            continue;
+        }
+        const float G = gk[l] * v.q;
+        const size_t pix = (size_t)v.y * p.W + v.x;
+        atomicAdd(&p.A[plane * l + pix], cl[l] * G);
+        atomicAdd(&p.A[plane * (l + 1) + pix], -cl[l] * G);
+        atomicAdd(&dc[l], gk[l] * v.qe);
+        atomicAdd(&dt[l], v.s * gdk[l]);
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < p.P; l += blockDim.x) {
+        if (dc[l] != 0.0f) atomicAdd(&p.dc_acc[l], (double)dc[l]);
+        if (dt[l] != 0.0f) atomicAdd(&p.dt_acc[l], (double)dt[l]);
+    }
+}
+
+static int adjoint_tail(dog_handle* h, SoftWS* ws, const SoftPrep& q, const float* img, int H, int W, int pitch,
+                        const float* sig, float* gimg, float* gsig, cudaStream_t s);
+
 int soft_backward(dog_handle* h, const float* img, int H, int W, int pitch, const float* sig,
                   const float* gH, float* gimg, float* gsig, cudaStream_t s) {
     SoftWS* ws = nullptr;
@@ -658,6 +729,49 @@ int soft_backward(dog_handle* h, const float* img, int H, int W, int pitch, cons
     p.dt_acc = ws->acc + P;
     SOFT_CUDA(timed_fused(h, p, p.n_strips * p.n_bands, s));
     SOFT_CUDA(launch_resolve(soft_resolve(h, p), std::min(ws->pend_cap, 152 * 64), s));
+    return adjoint_tail(h, ws, q, img, H, W, pitch, sig, gimg, gsig, s);
+}
+
+int soft_backward_rec(dog_handle* h, const float* img, int H, int W, int pitch, const float* sig,
+                      const dog_soft_max* rec, const int* rec_count, int rec_cap, const float* gH, float* gimg,
+                      float* gsig, cudaStream_t s) {
+    SoftWS* ws = nullptr;
+    int st = soft_ws(h, H, W, &ws);
+    if (st != DOG_OK) return st;
+    SoftPrep q = prep_params(h, ws, sig);
+    soft_prep_kernel<<<1, PREP_THREADS, 0, s>>>(q);
+    SOFT_CUDA(cudaGetLastError());
+    const FusedParams& b = handle_base(h);
+    const int K = b.K, P = b.P;
+    SOFT_CUDA(cudaMemsetAsync(ws->acc, 0, sizeof(double) * (2 * P + K), s));
+    SOFT_CUDA(cudaMemsetAsync(ws->A, 0, sizeof(float) * (size_t)K * H * W, s));
+    ScatterParams c{};
+    c.rec = rec;
+    c.count = rec_count;
+    c.cap = rec_cap;
+    c.gH = gH;
+    c.kappa = ws->kappa;
+    c.dkappa = ws->dkappa;
+    c.c = ws->c;
+    c.P = P;
+    c.nbins = handle_cfg(h).nbins;
+    c.H = H;
+    c.W = W;
+    c.A = ws->A;
+    c.dc_acc = ws->acc;
+    c.dt_acc = ws->acc + P;
+    c.status = handle_status(h);
+    const int grid = std::max(1, std::min((rec_cap + 255) / 256, 152 * 8));
+    soft_scatter_kernel<<<grid, 256, 0, s>>>(c);
+    SOFT_CUDA(cudaGetLastError());
+    return adjoint_tail(h, ws, q, img, H, W, pitch, sig, gimg, gsig, s);
+}
+
+// The adjoint blurs of the dloss/dL planes in ws->A, then the sigma gradient.
+static int adjoint_tail(dog_handle* h, SoftWS* ws, const SoftPrep& q, const float* img, int H, int W, int pitch,
+                        const float* sig, float* gimg, float* gsig, cudaStream_t s) {
+    const FusedParams& b = handle_base(h);
+    const int K = b.K, P = b.P;
     AdjParams a{};
     a.A = ws->A;
     a.Y = ws->Y;

@@ -253,23 +253,39 @@ class Detector:
 
     # --------------------------------------------------------- differentiable
     def soft_hist(self, img: torch.Tensor, sigmas: torch.Tensor, out: torch.Tensor | None = None,
-                  stream=None) -> torch.Tensor:
+                  stream=None, rec: "SoftMaxima | None" = None) -> torch.Tensor:
+        """Soft histogram (accumulated into `out`); with `rec`, the maxima are
+        recorded for `backward(..., rec=rec)`."""
         H, W, pitch = _check_img(img)
         if out is None:
             out = torch.zeros(self.cfg.nbins, dtype=torch.float32, device=img.device)
-        check(self.lib.dog_soft_hist(self.h, img.data_ptr(), H, W, pitch, sigmas.data_ptr(), out.data_ptr(),
-                                     _stream(stream)), "dog_soft_hist")
+        if rec is None:
+            check(self.lib.dog_soft_hist(self.h, img.data_ptr(), H, W, pitch, sigmas.data_ptr(), out.data_ptr(),
+                                         _stream(stream)), "dog_soft_hist")
+        else:
+            check(self.lib.dog_soft_hist_rec(self.h, img.data_ptr(), H, W, pitch, sigmas.data_ptr(),
+                                             out.data_ptr(), rec.buf.data_ptr(), rec.cap, rec.count.data_ptr(),
+                                             _stream(stream)), "dog_soft_hist_rec")
         return out
 
     def backward(self, img: torch.Tensor, sigmas: torch.Tensor, grad_hist: torch.Tensor,
-                 grad_sigmas: torch.Tensor | None = None, stream=None):
+                 grad_sigmas: torch.Tensor | None = None, stream=None, rec: "SoftMaxima | None" = None):
+        """dloss/dI and (accumulated) dloss/dsigma.  With `rec` (a complete
+        record of this frame's forward at the same sigmas) the dloss/dL planes
+        come from the recorded maxima; otherwise the blur levels are
+        recomputed."""
         H, W, pitch = _check_img(img)
         gi = torch.empty((H, W), dtype=torch.float32, device=img.device)
         gs = grad_sigmas if grad_sigmas is not None else torch.zeros(self.K, dtype=torch.float32,
                                                                    device=img.device)
-        check(self.lib.dog_backward(self.h, img.data_ptr(), H, W, pitch, sigmas.data_ptr(),
-                                    grad_hist.contiguous().data_ptr(), gi.data_ptr(), gs.data_ptr(),
-                                    _stream(stream)), "dog_backward")
+        g = grad_hist.contiguous()
+        if rec is None:
+            check(self.lib.dog_backward(self.h, img.data_ptr(), H, W, pitch, sigmas.data_ptr(),
+                                        g.data_ptr(), gi.data_ptr(), gs.data_ptr(), _stream(stream)), "dog_backward")
+        else:
+            check(self.lib.dog_backward_rec(self.h, img.data_ptr(), H, W, pitch, sigmas.data_ptr(),
+                                            rec.buf.data_ptr(), rec.count.data_ptr(), rec.cap, g.data_ptr(),
+                                            gi.data_ptr(), gs.data_ptr(), _stream(stream)), "dog_backward_rec")
         return gi, gs
 
 
@@ -280,32 +296,55 @@ def blobs_from_raw(raw: torch.Tensor, count: int):
     return ints[:, 0], ints[:, 1], ints[:, 2], flt[:, 0], flt[:, 1]
 
 
+class SoftMaxima:
+    """Device list of the hard local maxima one soft-histogram forward found
+    (`dog_soft_max` records, 24 bytes each) and its true count."""
+
+    def __init__(self, cap: int, device):
+        self.cap = int(cap)
+        self.buf = torch.empty((self.cap, 6), dtype=torch.int32, device=device)
+        self.count = torch.zeros((), dtype=torch.int32, device=device)
+
+
 class DoGSoftHist(torch.autograd.Function):
     """Soft blob-volume histogram of a batch of frames with learnable sigmas.
 
     forward(frames (B, H, W) float32 CUDA, sigmas (K,) float32 CUDA, det) ->
-    H (nbins,) summed over the batch.  backward recomputes the blur levels in
-    the CUDA kernels (nothing is saved but the inputs)."""
+    H (nbins,) summed over the batch.  The forward records each frame's hard
+    maxima (O(maxima) memory, no blur level is kept); backward scatters the
+    dloss/dL planes from them and runs the adjoint blurs.  A frame whose list
+    overflowed (more maxima than `rec_cap`, e.g. a flat frame where every
+    voxel ties) recomputes its blur levels in the backward instead."""
+
+    rec_cap = 1 << 18
 
     @staticmethod
     def forward(ctx, frames: torch.Tensor, sigmas: torch.Tensor, det: Detector):
         frames = frames.contiguous()
         sig = sigmas.detach().contiguous()
         out = torch.zeros(det.cfg.nbins, dtype=torch.float32, device=frames.device)
+        grads = any(ctx.needs_input_grad[:2])
+        recs = [SoftMaxima(DoGSoftHist.rec_cap, frames.device) if grads else None for _ in range(frames.shape[0])]
         for b in range(frames.shape[0]):
-            det.soft_hist(frames[b], sig, out=out)
+            det.soft_hist(frames[b], sig, out=out, rec=recs[b])
         ctx.save_for_backward(frames, sig)
         ctx.det = det
+        ctx.recs = recs
         return out
 
     @staticmethod
     def backward(ctx, grad_out: torch.Tensor):
         frames, sig = ctx.saved_tensors
         det = ctx.det
+        recs = ctx.recs
+        counts = torch.stack([r.count for r in recs]).cpu().tolist()   # one sync per batch
+        if any(c > r.cap for c, r in zip(counts, recs)):
+            det.status()   # clears the capacity flag of the overflowed record
         gs = torch.zeros(det.K, dtype=torch.float32, device=frames.device)
         gimg = torch.empty_like(frames)
         g = grad_out.contiguous().float()
         for b in range(frames.shape[0]):
-            gi, _ = det.backward(frames[b], sig, g, grad_sigmas=gs)
+            rec = recs[b] if counts[b] <= recs[b].cap else None
+            gi, _ = det.backward(frames[b], sig, g, grad_sigmas=gs, rec=rec)
             gimg[b].copy_(gi)
         return gimg, gs, None
