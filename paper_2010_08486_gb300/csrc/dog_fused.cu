@@ -494,22 +494,10 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                     }
                 }
             } else if (mode == MODE_SOFT) {
-                // optional record of the maxima for the backward: one slot
-                // reservation per row, as for candidates
+                // optional record of the maxima for the backward: each lane
+                // with maxima reserves its slots (about one lane per warp row)
                 int idx = 0;
-                if (p.rec != nullptr) {
-                    const int nmine = __popc(dmask);
-                    int incl = nmine;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += t;
-                    }
-                    const int total = __shfl_sync(0xffffffffu, incl, 31);
-                    int base = 0;
-                    if (lane == 0 && total) base = atomicAdd(p.rec_count, total);
-                    idx = __shfl_sync(0xffffffffu, base, 0) + incl - nmine;
-                }
+                if (p.rec != nullptr && dmask != 0u) idx = atomicAdd(p.rec_count, __popc(dmask));
                 unsigned rest = dmask;
                 while (rest) {
                     const int l = __ffs(rest) - 1;

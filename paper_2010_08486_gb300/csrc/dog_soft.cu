@@ -480,23 +480,25 @@ __global__ void __launch_bounds__(128) adj_y_fold_kernel(const __grid_constant__
     p.Yd[o] += adj1d_mirror(A, p.W, p.H, m, p.dw + p.woff[i], r);
 }
 
-// Reflect fold of the row adjoint: columns within R of the left or right edge
-// (blockIdx.x-th of them), one thread per row; sums the reflected preimages'
-// part over every level whose radius reaches the column.
+// Reflect fold of the row adjoint: one warp per row y, its lanes on the
+// columns within R of the left or right edge (so a warp's loads fall in the
+// same few cache lines of that row); sums the reflected preimages' part over
+// every level whose radius reaches the column.
 __global__ void __launch_bounds__(128) adj_x_fold_kernel(const __grid_constant__ AdjParams p) {
-    const int j = blockIdx.x;
-    if (j >= fold_count(p.W, p.R)) return;
-    const int x = fold_index(p.W, p.R, j);
-    const int y = blockIdx.y * blockDim.x + threadIdx.x;
+    const int y = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (y >= p.H) return;
     const size_t plane = (size_t)p.H * p.W;
-    float v = 0.0f;
-    for (int i = 0; i < p.K; ++i) {
-        const int r = p.r[i];
-        if (x >= r && x <= p.W - 1 - r) continue;
-        v += adj1d_mirror(p.Y + plane * i + (size_t)y * p.W, 1, p.W, x, p.w + p.woff[i], r);
+    const int nf = fold_count(p.W, p.R);
+    for (int j = threadIdx.x & 31; j < nf; j += 32) {
+        const int x = fold_index(p.W, p.R, j);
+        float v = 0.0f;
+        for (int i = 0; i < p.K; ++i) {
+            const int r = p.r[i];
+            if (x >= r && x <= p.W - 1 - r) continue;
+            v += adj1d_mirror(p.Y + plane * i + (size_t)y * p.W, 1, p.W, x, p.w + p.woff[i], r);
+        }
+        p.gimg[(size_t)y * p.W + x] += v;
     }
-    p.gimg[(size_t)y * p.W + x] += v;
 }
 
 constexpr int ADJ_XR = 32;     // output rows per CTA of the row adjoint (4 warps x 8)
@@ -802,8 +804,7 @@ static int adjoint_tail(dog_handle* h, SoftWS* ws, const SoftPrep& q, const floa
     dim3 gx((W + 31) / 32, (H + ADJ_XR - 1) / ADJ_XR);
     adj_x_kernel<<<gx, 128, sizeof(float) * adj_x_smem_floats(tpad_max, b.R), s>>>(a, tpad_max);
     SOFT_CUDA(cudaGetLastError());
-    dim3 gxf(fold_count(W, b.R), (H + 127) / 128);
-    adj_x_fold_kernel<<<gxf, 128, 0, s>>>(a);
+    adj_x_fold_kernel<<<(H + 3) / 4, 128, 0, s>>>(a);
     SOFT_CUDA(cudaGetLastError());
     FinParams f{};
     f.sig = sig;
