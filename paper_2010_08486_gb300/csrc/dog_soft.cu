@@ -494,23 +494,66 @@ __global__ void __launch_bounds__(128) adj_y_fold_kernel(const __grid_constant__
 }
 
 // Reflect fold of the row adjoint: one warp per row y, its lanes on the
-// columns within R of the left or right edge (so a warp's loads fall in the
-// same few cache lines of that row); sums the reflected preimages' part over
-// every level whose radius reaches the column.
-__global__ void __launch_bounds__(128) adj_x_fold_kernel(const __grid_constant__ AdjParams p) {
-    const int y = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+// columns within R of the left or right edge; sums the reflected preimages'
+// part over every level whose radius reaches the column.  When the frame is
+// wider than 2R, a level's reflected terms read only the first and last r_i
+// values of the row, which the warp first stages in shared memory (one round
+// of coalesced loads per level instead of a serial chain of global loads).
+constexpr int FOLD_ROWS = 4;   // warps (rows) per CTA
+__global__ void __launch_bounds__(32 * FOLD_ROWS) adj_x_fold_kernel(const __grid_constant__ AdjParams p) {
+    __shared__ float edge[FOLD_ROWS][2][DOG_MAX_RADIUS];
+    const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int y = blockIdx.x * FOLD_ROWS + wq;
     if (y >= p.H) return;
     const size_t plane = (size_t)p.H * p.W;
     const int nf = fold_count(p.W, p.R);
-    for (int j = threadIdx.x & 31; j < nf; j += 32) {
-        const int x = fold_index(p.W, p.R, j);
-        float v = 0.0f;
-        for (int i = 0; i < p.K; ++i) {
-            const int r = p.r[i];
-            if (x >= r && x <= p.W - 1 - r) continue;
-            v += adj1d_mirror(p.Y + plane * i + (size_t)y * p.W, 1, p.W, x, p.w + p.woff[i], r);
+    if (p.W <= 2 * p.R) {   // narrow frame: several reflections, gather from global memory
+        for (int j = lane; j < nf; j += 32) {
+            const int x = fold_index(p.W, p.R, j);
+            float v = 0.0f;
+            for (int i = 0; i < p.K; ++i) {
+                const int r = p.r[i];
+                if (x >= r && x <= p.W - 1 - r) continue;
+                v += adj1d_mirror(p.Y + plane * i + (size_t)y * p.W, 1, p.W, x, p.w + p.woff[i], r);
+            }
+            p.gimg[(size_t)y * p.W + x] += v;
         }
-        p.gimg[(size_t)y * p.W + x] += v;
+        return;
+    }
+    float* sl = edge[wq][0];   // Y_i(y, 0 .. r-1)
+    float* sr = edge[wq][1];   // Y_i(y, W-r .. W-1)
+    float v[(2 * DOG_MAX_RADIUS + 31) / 32];
+#pragma unroll
+    for (int k = 0; k < (2 * DOG_MAX_RADIUS + 31) / 32; ++k) v[k] = 0.0f;
+    for (int i = 0; i < p.K; ++i) {
+        const int r = p.r[i];
+        const float* row = p.Y + plane * i + (size_t)y * p.W;
+        __syncwarp();
+        for (int n = lane; n < r; n += 32) {
+            sl[n] = row[n];
+            sr[n] = row[p.W - r + n];
+        }
+        __syncwarp();
+        const float* w = p.w + p.woff[i];   // w[r + d] weighs offset d
+#pragma unroll
+        for (int k = 0; k < (2 * DOG_MAX_RADIUS + 31) / 32; ++k) {
+            const int j = lane + 32 * k;
+            if (j >= nf) break;
+            const int x = fold_index(p.W, p.R, j);
+            float acc = 0.0f;
+            if (x < r) {   // reflected copy q = -1 - x: sum_{n=0}^{r-1-x} w[r + q - n] Y(n)
+                for (int n = 0; n <= r - 1 - x; ++n) acc = __fmaf_rn(__ldg(w + r - 1 - x - n), sl[n], acc);
+            } else if (x > p.W - 1 - r) {   // q = 2W - 1 - x: sum_{n=q-r}^{W-1} w[r + q - n] Y(n)
+                const int q = 2 * p.W - 1 - x;
+                for (int n = q - r; n <= p.W - 1; ++n) acc = __fmaf_rn(__ldg(w + r + q - n), sr[n - (p.W - r)], acc);
+            }
+            v[k] += acc;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < (2 * DOG_MAX_RADIUS + 31) / 32; ++k) {
+        const int j = lane + 32 * k;
+        if (j < nf) p.gimg[(size_t)y * p.W + fold_index(p.W, p.R, j)] += v[k];
     }
 }
 
@@ -1016,7 +1059,7 @@ static int adjoint_tail(dog_handle* h, SoftWS* ws, const SoftPrep& q, const floa
         adj_x_kernel<false><<<gx, 128, sizeof(float) * adj_x_smem_floats(tpad_max, b.R, false), s>>>(a, tpad_max);
     }
     SOFT_CUDA(cudaGetLastError());
-    adj_x_fold_kernel<<<(H + 3) / 4, 128, 0, s>>>(a);
+    adj_x_fold_kernel<<<(H + FOLD_ROWS - 1) / FOLD_ROWS, 32 * FOLD_ROWS, 0, s>>>(a);
     SOFT_CUDA(cudaGetLastError());
     FinParams f{};
     f.sig = sig;
