@@ -54,6 +54,8 @@ def parse():
                     help="length of the 8-stream serving run (0: skip)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched-uneven and differentiable legs")
+    ap.add_argument("--leg", choices=["batched", "differentiable"], default=None,
+                    help="run only this form and print its JSON object (a profiling entry point)")
     return ap.parse_args()
 
 
@@ -548,8 +550,21 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_leg(a):
+    import torch
+    from paper_2010_08486_gb300 import build as libbuild
+    libbuild.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    res = batched_leg(local, a.tune_cache) if a.leg == "batched" else diff_leg(local)
+    print(json.dumps({"leg": a.leg, **res}))
+
+
 def main():
     a = parse()
+    if a.leg:
+        run_leg(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:
