@@ -129,6 +129,16 @@ def measured_peaks():
         return {}
 
 
+def fused_kernel_sha():
+    """sha256 over the fused kernel's sources (kernel file, device helpers,
+    shared parameter header), in that order."""
+    h = hashlib.sha256()
+    for f in ("dog_fused.cu", "dog_device.cuh", "dog_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2010_08486_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def fused_traffic(frames_per_launch):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     scaled to this launch by frames; None if the kernel changed since."""
@@ -136,8 +146,7 @@ def fused_traffic(frames_per_launch):
     try:
         with open(path) as f:
             rec = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2010_08486_gb300", "csrc", "dog_fused.cu"), "rb").read()
-        if rec.get("kernel_sha256") != hashlib.sha256(src).hexdigest():
+        if rec.get("kernel_sha256") != fused_kernel_sha():
             return None
         return rec["dram_bytes_per_frame"] * frames_per_launch
     except (OSError, KeyError, ValueError):

@@ -1,0 +1,37 @@
+// Device helpers shared by the detection kernels (sm_103a): the reflect
+// boundary, pixel ingest and the DoG value, so that the fused kernel and the
+// strip-edge resolve form every value with the same operations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dog.h"
+
+namespace dogk {
+
+// Half-sample-symmetric reflection of index i into [0, n): -1 -> 0,
+// -k -> k-1, n+k -> n-1-k, folded with period 2n for any i.
+__device__ __forceinline__ int refl(int i, int n) {
+    if (i >= 0 && i < n) return i;
+    int p = 2 * n;
+    int m = i % p;
+    if (m < 0) m += p;
+    return m >= n ? p - 1 - m : m;
+}
+
+// Raw pixel load and its conversion to [0, 1] (uint16 counts: one IEEE
+// division by 4095).
+__device__ __forceinline__ unsigned load_raw(const void* img, int dtype, int pitch, int y, int x) {
+    if (dtype == DOG_DTYPE_U16)
+        return (unsigned)__ldg(reinterpret_cast<const unsigned short*>(img) + (size_t)y * pitch + x);
+    return __float_as_uint(__ldg(reinterpret_cast<const float*>(img) + (size_t)y * pitch + x));
+}
+__device__ __forceinline__ float raw_to_px(unsigned v, int dtype) {
+    return dtype == DOG_DTYPE_U16 ? __fdiv_rn((float)v, 4095.0f) : __uint_as_float(v);
+}
+
+__device__ __forceinline__ float dog_value(float c, float a, float b) {
+    return __fmul_rn(c, __fsub_rn(a, b));
+}
+
+}  // namespace dogk
