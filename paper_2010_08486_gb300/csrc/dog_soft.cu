@@ -618,9 +618,40 @@ __global__ void __launch_bounds__(128) adj_x_kernel(const __grid_constant__ AdjP
             wd[t] = p.dw[p.woff[i] + t];
         }
         const int wt = 32 + tpad + 8;
-        {   // Y_i rows y0 .. y0+31, columns x0-r .. x0-r+wt-1 (zero outside the frame)
+        // Y_i rows y0 .. y0+31, columns x0-r .. x0-r+wt-1 (zero outside the frame)
+        const int xs = x0 - r;
+        const int xa = xs >= 0 ? xs & ~3 : -((3 - xs) & ~3);   // xs rounded down to a multiple of 4
+        const int off = xs - xa, n4 = (wt + off + 3) >> 2;     // float4 columns per row
+        if ((p.W & 3) == 0 && xa >= 0 && xa + 4 * n4 <= p.W && y0 + ADJ_XR <= p.H) {
+            // interior tile: 16-byte loads, thread (row phase, float4 column),
+            // four rows' loads in flight
+            const int rpp = 128 / n4, r0 = threadIdx.x / n4, c4 = threadIdx.x - r0 * n4;
+            if (r0 < rpp) {
+                const float4* src = reinterpret_cast<const float4*>(Yi + (size_t)y0 * p.W + xa) + c4;
+                const int row4 = p.W >> 2;
+                for (int rb = r0; rb < ADJ_XR; rb += 4 * rpp) {
+                    float4 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int rr = min(rb + u * rpp, ADJ_XR - 1);
+                        v[u] = __ldg(src + (size_t)rr * row4);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int rr = rb + u * rpp;
+                        if (rr < ADJ_XR) {
+                            float* d = Yt + rr * SY + 4 * c4 - off;   // column 4 c4 + k - off of the tile
+                            const float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (4 * c4 + k - off >= 0 && 4 * c4 + k - off < wt) d[k] = e[k];
+                        }
+                    }
+                }
+            }
+        } else {
             const int c0 = threadIdx.x, c1 = threadIdx.x + 128;
-            const int xx0 = x0 - r + c0, xx1 = x0 - r + c1;
+            const int xx0 = xs + c0, xx1 = xs + c1;
             const bool ok0 = c0 < wt && xx0 >= 0 && xx0 < p.W, ok1 = c1 < wt && xx1 >= 0 && xx1 < p.W;
             for (int rr0 = 0; rr0 < ADJ_XR; rr0 += 8) {   // 16 loads in flight before the stores
                 float v0[8], v1[8];
