@@ -12,8 +12,13 @@
 //   dloss/dI = sum_i B_i^T A_i,     B_i = row blur o column blur (reflect)
 //   dloss/dsigma_i = <B_y^T A_i, B_x' I> + <B_y'^T A_i, B_x I>  (kernel shape)
 //                  + dloss/dc terms + dloss/dt terms.
-// The forward L_i are recomputed by the fused kernel (MODE_BWD), which also
-// writes A densely; the adjoint blurs gather through the reflect fold-back.
+// Two backward paths.  From a record of the forward's maxima (soft forward
+// with `rec`): A is scattered from the list, and the kernel-shape term is
+// evaluated at the maxima as sum_v A_i(v) dL_i/dsigma_i(v) (the same sum,
+// since A_i vanishes elsewhere); no blur level is formed.  Without a record:
+// the fused kernel (MODE_BWD) recomputes the L_i and writes A densely, and
+// the kernel-shape term is the two inner products above.  Both then run the
+// adjoint blurs, which gather through the reflect fold-back.
 #include <cuda_runtime.h>
 
 #include <algorithm>
