@@ -88,6 +88,32 @@ def test_backward_matches_oracle_gradient(n, use_rec):
     assert np.linalg.norm(gs - osg) <= 1e-4 * np.linalg.norm(osg)
 
 
+@pytest.mark.parametrize("use_rec", [False, True])
+def test_backward_odd_shape_matches_oracle(use_rec):
+    # width not a multiple of 4 (no vectorised staging), height not a multiple
+    # of the adjoint tiles, both wider than 2 R (one reflected copy per edge)
+    img = synth.plif_frame(synth.GRAD_SEED_BASE + 5)[300:450, 400:573].copy()
+    cfg, det, p, sig0, sig = setup(img)
+    t = torch.from_numpy(img).cuda()
+    s = torch.from_numpy(sig).cuda()
+    rad = np.asarray(det.radii)
+    mask = gpu_mask(det, t, sig)
+    Ho = oracle.soft_hist(img.astype(np.float64), sig.astype(np.float64), rad, p, sig0, mask)
+    gH = (2.0 * (Ho - 0.5 * Ho.mean())).astype(np.float32)
+    rec = None
+    if use_rec:
+        rec = dog.SoftMaxima(1 << 16, "cuda")
+        det.soft_hist(t, s, rec=rec)
+        assert 0 < int(rec.count) <= rec.cap and det.status() == 0
+    gi, gs = det.backward(t, s, torch.from_numpy(gH).cuda(), rec=rec)
+    assert det.status() == 0
+    gi, gs = gi.cpu().numpy().astype(np.float64), gs.cpu().numpy().astype(np.float64)
+    oi, osg = oracle.soft_grad(img.astype(np.float64), sig.astype(np.float64), rad, p, sig0,
+                               gH.astype(np.float64), mask)
+    assert np.linalg.norm(gi - oi) <= 1e-4 * np.linalg.norm(oi)
+    assert np.linalg.norm(gs - osg) <= 1e-4 * np.linalg.norm(osg)
+
+
 def test_autograd_function_matches_backward():
     imgs = np.stack([crop(synth.GRAD_SEED_BASE + f, n=96) for f in range(3)])
     cfg, det, p, sig0, sig = setup(imgs[0])
