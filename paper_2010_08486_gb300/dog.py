@@ -259,6 +259,8 @@ class Detector:
         H, W, pitch = _check_img(img)
         if out is None:
             out = torch.zeros(self.cfg.nbins, dtype=torch.float32, device=img.device)
+        if rec is not None:
+            _check_rec(rec, img.device)
         if rec is None:
             check(self.lib.dog_soft_hist(self.h, img.data_ptr(), H, W, pitch, sigmas.data_ptr(), out.data_ptr(),
                                          _stream(stream)), "dog_soft_hist")
@@ -279,6 +281,8 @@ class Detector:
         gs = grad_sigmas if grad_sigmas is not None else torch.zeros(self.K, dtype=torch.float32,
                                                                    device=img.device)
         g = grad_hist.contiguous()
+        if rec is not None:
+            _check_rec(rec, img.device)
         if rec is None:
             check(self.lib.dog_backward(self.h, img.data_ptr(), H, W, pitch, sigmas.data_ptr(),
                                         g.data_ptr(), gi.data_ptr(), gs.data_ptr(), _stream(stream)), "dog_backward")
@@ -294,6 +298,12 @@ def blobs_from_raw(raw: torch.Tensor, count: int):
     ints = r[:, :3].numpy()
     flt = r[:, 3:].view(torch.float32).numpy()
     return ints[:, 0], ints[:, 1], ints[:, 2], flt[:, 0], flt[:, 1]
+
+
+def _check_rec(rec: "SoftMaxima", device) -> None:
+    if (rec.buf.dtype != torch.int32 or tuple(rec.buf.shape) != (rec.cap, 6) or not rec.buf.is_contiguous()
+            or rec.buf.device != device or rec.count.device != device or rec.count.dtype != torch.int32):
+        raise ValueError("SoftMaxima: int32 (cap, 6) record and int32 count on the frame's device expected")
 
 
 class SoftMaxima:
@@ -339,7 +349,10 @@ class DoGSoftHist(torch.autograd.Function):
         recs = ctx.recs
         counts = torch.stack([r.count for r in recs]).cpu().tolist()   # one sync per batch
         if any(c > r.cap for c, r in zip(counts, recs)):
-            det.status()   # clears the capacity flag of the overflowed record
+            # the overflowed record set the capacity flag; anything else is an error
+            st = det.status()
+            if st not in (0, _lib.DOG_ERR_CAPACITY):
+                check(st, "dog_soft_hist_rec")
         gs = torch.zeros(det.K, dtype=torch.float32, device=frames.device)
         gimg = torch.empty_like(frames)
         g = grad_out.contiguous().float()
