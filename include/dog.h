@@ -164,12 +164,14 @@ int dog_prune(dog_t* h, const dog_blob* d_cand, const int32_t* d_count, int32_t 
 /* Pruning without a handle and without allocating anything.  The paper has
  * no counterpart: this is a convenience for callers that may not allocate
  * device memory themselves, such as a plug-in whose host framework owns all
- * device memory and forbids allocations inside its execution step, or code
- * that runs between stream-capture calls where a cudaMalloc would break the
- * recorded sequence.  Same result as dog_prune for the same candidate list.
+ * device memory and forbids allocations inside its execution step, or a
+ * real-time loop that must not stall on the allocator.  Same result as
+ * dog_prune for the same candidate list.
  *
  *  h_sigmas   the n_planes DoG-plane sigmas (host, increasing), i.e. the
- *             ladder's first K-1 values; candidate levels index them.
+ *             ladder's first K-1 values; candidate levels index them.  Read
+ *             on the host during the call (passed to the GPU as a kernel
+ *             parameter), so the caller may reuse the array on return.
  *  overlap    threshold on the normalised disc overlap, in [0, 1).
  *  mode       DOG_PRUNE_COALESCE, DOG_PRUNE_SUPPRESS or DOG_PRUNE_OFF.
  *  d_cand, d_count, cap_in, d_out, cap_out, d_nout   as in dog_prune.
@@ -180,9 +182,12 @@ int dog_prune(dog_t* h, const dog_blob* d_cand, const int32_t* d_count, int32_t 
  * returns DOG_ERR_UNSUPPORTED.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before
  * any stream capture.  All calls share the array and it keeps the last
- * call's contents, so calls whose GPU work may overlap (other streams, other
- * host threads) race: serialise them on one stream.  Overflow of cap_out is
- * reported through *d_nout (the true count), not through a handle status. */
+ * call's contents (each call rewrites its tables and the per-candidate
+ * state), so calls whose GPU work may overlap (other streams, other host
+ * threads) race: serialise them on one stream.  There is no handle and no
+ * status word to read: overflow of cap_out shows only as *d_nout > cap_out
+ * (the true count), and errors of the launch itself come back as the return
+ * code. */
 #define DOG_NOALLOC_MAX_CAND 65536
 int dog_prune_noalloc(const dog_blob* d_cand, const int32_t* d_count, int32_t cap_in,
                       const double* h_sigmas, int32_t n_planes, double overlap, int32_t mode,
@@ -294,6 +299,17 @@ int dog_ring_hist_push_batched(const uint32_t* d_hists, const int32_t* d_stream_
  * number of timed launches, and clears them. */
 int dog_profile_enable(dog_t* h, int32_t enable);
 int dog_profile_read(dog_t* h, double* h_ms, int32_t* h_launches);
+
+/* Measured single-precision multiply-add peak of the current GPU, the
+ * roofline denominator of the detection kernels (no counterpart in the
+ * paper).  A grid of 4 CTAs x 256 threads per SM runs 16 independent FMA
+ * chains per thread from registers, `iters` x 64 FMAs per thread; pair != 0
+ * issues them as packed two-lane FMAs (two per instruction).  The launch is
+ * timed `reps` times with CUDA events on `stream` after one short warm-up;
+ * *h_tflops receives the median rate (2 flop per FMA), *h_ms (NULL ok) the
+ * median launch time.  Allocates and frees 4 bytes of device memory;
+ * synchronises the stream. */
+int dog_fma_peak(int32_t pair, int64_t iters, int32_t reps, double* h_tflops, double* h_ms, void* stream);
 
 /* Read and clear the handle's device status word (synchronises the stream
  * passed to the last call).  *h_status receives DOG_OK or the first error. */

@@ -44,7 +44,10 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", "-D_GNU_SOURCE",
+    # -ffp-contract=off: every a*b+c rounds twice, as written, on every host
+    # (gcc for aarch64 would otherwise fuse them), so the oracle gives the same
+    # doubles on x86-64 and Arm; no -march=native for the same reason.
+    cmd = ["gcc", "-O3", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp", "-std=c11", "-D_GNU_SOURCE",
            _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -60,6 +63,12 @@ def _load():
         P = ctypes.POINTER
         d, i, u8 = ctypes.c_double, ctypes.c_int, ctypes.c_uint8
         dp, ip, i32p = P(d), P(i), P(ctypes.c_int32)
+        u16p = P(ctypes.c_uint16)
+        lib.ora_stretch_rank.argtypes = [ctypes.c_long, d]
+        lib.ora_stretch_rank.restype = ctypes.c_long
+        lib.ora_stretch_limits.argtypes = [u16p, ctypes.c_long, d, i32p, i32p]
+        lib.ora_stretch_limits.restype = i
+        lib.ora_stretch.argtypes = [u16p, ctypes.c_long, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_float)]
         lib.ora_num_threads.restype = i
         lib.ora_reflect.argtypes = [ctypes.c_long, ctypes.c_long]
         lib.ora_reflect.restype = ctypes.c_long
@@ -414,3 +423,41 @@ def continuum_peak_response(amp: float, ratio: float) -> float:
 def continuum_centre_response(amp: float, s: float, sig: float, ratio: float) -> float:
     return amp * s * s * sig * sig * (ratio + 1.0) / ((s * s + sig * sig) * (s * s + ratio * ratio * sig * sig))
 
+
+
+# ---------------------------------------------------------------------------
+# Preprocessing: contrast stretch with saturation (Sec. 4, first, optional
+# step; 0.35% in the paper).
+
+def stretch_rank(n: int, sat: float) -> int:
+    """k = floor(sat / 2 * n): the rank (0-based, ascending) of the count that
+    maps to 0; rank n - 1 - k maps to 1."""
+    return int(_load().ora_stretch_rank(int(n), float(sat)))
+
+
+def stretch_limits(counts, sat: float = 0.0035):
+    """(lo, hi) of a frame of 12-bit counts (values above 4095 count as 4095):
+    the counts at ranks k and n - 1 - k of the sorted frame."""
+    c = np.ascontiguousarray(counts, dtype=np.uint16).ravel()
+    lo, hi = ctypes.c_int32(), ctypes.c_int32()
+    rc = _load().ora_stretch_limits(c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)), c.size, float(sat),
+                                   ctypes.byref(lo), ctypes.byref(hi))
+    if rc != 0:
+        raise ValueError("stretch_limits failed (%d)" % rc)
+    return lo.value, hi.value
+
+
+def stretch(counts, lo: int, hi: int) -> np.ndarray:
+    """The stretched frame in [0, 1] (float32): (c - lo) / (hi - lo) in double,
+    clipped, rounded to float."""
+    c = np.ascontiguousarray(counts, dtype=np.uint16)
+    out = np.empty(c.shape, dtype=np.float32)
+    _load().ora_stretch(c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)), c.size, int(lo), int(hi),
+                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    return out
+
+
+def preprocess(counts, sat: float = 0.0035) -> np.ndarray:
+    """Contrast-stretched frame with the frame's own limits."""
+    lo, hi = stretch_limits(counts, sat)
+    return stretch(counts, lo, hi)

@@ -558,3 +558,48 @@ void ora_soft_grad(const double* img, int h, int w, const double* sig, const int
     free(c);
     free(L);
 }
+
+/* ------------------------------------------------------------------------
+ * Preprocessing (Sec. 4, the optional first step; Table 2 times it): the
+ * frame is contrast stretched to [0, 1] with a saturation fraction `sat`
+ * (0.35% in the paper).  Reading: the saturation is split evenly between the
+ * two ends, so with the n counts sorted ascending, c_(0) <= ... <= c_(n-1),
+ * and k = floor(sat / 2 * n), the count c_(k) maps to 0, c_(n-1-k) maps to 1,
+ * and values outside are clipped.  Counts are 12-bit camera values; anything
+ * above 4095 is taken as 4095.  A frame whose two limits coincide maps to 0
+ * at or below the limit and 1 above it. */
+static int ora_int_cmp(const void* pa, const void* pb) {
+    const int a = *(const int*)pa, b = *(const int*)pb;
+    return (a > b) - (a < b);
+}
+
+long ora_stretch_rank(long n, double sat) { return (long)floor(sat * 0.5 * (double)n); }
+
+int ora_stretch_limits(const uint16_t* c, long n, double sat, int32_t* lo, int32_t* hi) {
+    if (n < 1) return -1;
+    int* v = (int*)malloc(sizeof(int) * (size_t)n);
+    if (!v) return -2;
+    for (long i = 0; i < n; ++i) v[i] = c[i] > 4095 ? 4095 : (int)c[i];
+    qsort(v, (size_t)n, sizeof(int), ora_int_cmp);
+    long k = ora_stretch_rank(n, sat);
+    if (k > (n - 1) / 2) k = (n - 1) / 2;
+    *lo = v[k];
+    *hi = v[n - 1 - k];
+    free(v);
+    return 0;
+}
+
+void ora_stretch(const uint16_t* c, long n, int32_t lo, int32_t hi, float* out) {
+    for (long i = 0; i < n; ++i) {
+        const int v = c[i] > 4095 ? 4095 : (int)c[i];
+        double t;
+        if (hi > lo) {
+            t = (double)(v - lo) / (double)(hi - lo);
+            if (t < 0.0) t = 0.0;
+            if (t > 1.0) t = 1.0;
+        } else {
+            t = v > lo ? 1.0 : 0.0;
+        }
+        out[i] = (float)t;
+    }
+}

@@ -33,7 +33,7 @@ EXPORTS = (
     "dog_config_default", "dog_create", "dog_destroy", "dog_ladder", "dog_candidates", "dog_prune",
     "dog_prune_noalloc", "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_soft_hist",
     "dog_backward", "dog_soft_hist_rec", "dog_backward_rec", "dog_debug_dog", "dog_ring_hist_push", "dog_ring_hist_push_batched",
-    "dog_profile_enable", "dog_profile_read",
+    "dog_profile_enable", "dog_profile_read", "dog_fma_peak",
     "dog_get_status", "dog_status_string",
 )
 
@@ -128,6 +128,7 @@ def load(path: str | None = None):
         lib.dog_ring_hist_push_batched.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp, vp]
         lib.dog_profile_enable.argtypes = [vp, i32]
         lib.dog_profile_read.argtypes = [vp, P(ctypes.c_double), P(i32)]
+        lib.dog_fma_peak.argtypes = [i32, ctypes.c_int64, i32, P(ctypes.c_double), P(ctypes.c_double), vp]
         lib.dog_get_status.argtypes = [vp, P(i32)]
         lib.dog_status_string.argtypes = [ctypes.c_int]
         lib.dog_status_string.restype = ctypes.c_char_p

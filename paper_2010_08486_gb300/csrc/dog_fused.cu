@@ -26,6 +26,8 @@
 // resolve kernel recomputes the few responses it needs.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "dog_internal.cuh"
 #include "dog_device.cuh"
 
@@ -669,23 +671,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
 }
 
 // The dynamic shared-memory limit is raised once per device and kernel form
-// (not on every launch, so launches can be captured into CUDA graphs).
-static int g_smem_limit[64][16];
+// (not on every launch, so launches can be captured into CUDA graphs); atomic
+// because handles on other host threads launch the same forms.
+static std::atomic<int> g_smem_limit[64][16];
 
 template <bool BATCHED, int PB, bool FULL>
-static cudaError_t launch_form(const FusedParams& p, int grid, cudaStream_t s, int* lim) {
-    if (*lim < p.smem_bytes) {
+static cudaError_t launch_form(const FusedParams& p, int grid, cudaStream_t s, std::atomic<int>* lim) {
+    if (lim->load(std::memory_order_acquire) < p.smem_bytes) {
         cudaError_t e = cudaFuncSetAttribute(dog_fused_kernel<BATCHED, PB, FULL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
         if (e != cudaSuccess) return e;
-        *lim = p.smem_bytes;
+        int cur = lim->load(std::memory_order_relaxed);
+        while (cur < p.smem_bytes && !lim->compare_exchange_weak(cur, p.smem_bytes)) {
+        }
     }
     dog_fused_kernel<BATCHED, PB, FULL><<<grid, NTHREADS, p.smem_bytes, s>>>(p);
     return cudaGetLastError();
 }
 
 template <bool BATCHED, int PB>
-static cudaError_t launch_bucket(const FusedParams& p, int grid, cudaStream_t s, int* lim) {
+static cudaError_t launch_bucket(const FusedParams& p, int grid, cudaStream_t s, std::atomic<int>* lim) {
     return p.P == PB ? launch_form<BATCHED, PB, true>(p, grid, s, lim + 1)
                      : launch_form<BATCHED, PB, false>(p, grid, s, lim);
 }
@@ -694,7 +699,7 @@ static cudaError_t launch_bucket(const FusedParams& p, int grid, cudaStream_t s,
 // 24 and MAX_LEVELS - 1 that holds P; a ladder that fills its bucket exactly
 // runs a form without the masks of planes past the ladder.
 template <bool BATCHED>
-static cudaError_t launch_planes(const FusedParams& p, int grid, cudaStream_t s, int* lim) {
+static cudaError_t launch_planes(const FusedParams& p, int grid, cudaStream_t s, std::atomic<int>* lim) {
     if (p.P <= 8) return launch_bucket<BATCHED, 8>(p, grid, s, lim + 0);
     if (p.P <= 16) return launch_bucket<BATCHED, 16>(p, grid, s, lim + 2);
     if (p.P <= 24) return launch_bucket<BATCHED, 24>(p, grid, s, lim + 4);
@@ -706,7 +711,7 @@ cudaError_t launch_fused(const FusedParams& p, int grid, cudaStream_t s) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    int* lim = g_smem_limit[dev & 63];
+    std::atomic<int>* lim = g_smem_limit[dev & 63];
     return p.frames != nullptr ? launch_planes<true>(p, grid, s, lim + 8) : launch_planes<false>(p, grid, s, lim);
 }
 

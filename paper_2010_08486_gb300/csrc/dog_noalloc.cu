@@ -8,14 +8,16 @@
 //
 // Host code cannot use the array's name as a device address; on each device,
 // the first call looks the address up with cudaGetSymbolAddress (with that
-// device current) and caches it.  Calls share the array, so calls whose GPU
+// device current) and caches it.  The per-call tables (conflict distances and
+// plane sigmas) are computed on the host and passed BY VALUE as a kernel
+// parameter to a one-CTA set-up kernel that writes them into the array, so no
+// call copies from host memory.  Calls share the array, so calls whose GPU
 // work overlaps (different streams, or other host threads) race on it; order
 // them on one stream.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <mutex>
-#include <vector>
 
 #include "dog_internal.cuh"
 
@@ -38,6 +40,20 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_lock;
 void* g_addr[kMaxDevices];   // device address of g_noalloc_scratch, per device
+
+// Per-call tables, passed by value (about 4.4 KB of kernel parameters).
+struct NoallocTables {
+    int d2[MAX_LEVELS * MAX_LEVELS];   // P x P conflict distances, row-major
+    double sig[MAX_LEVELS];            // plane sigmas
+    int P;
+};
+
+__global__ void noalloc_setup_kernel(const __grid_constant__ NoallocTables t, int* d2thr, double* sig,
+                                     int* status) {
+    for (int q = threadIdx.x; q < t.P * t.P; q += blockDim.x) d2thr[q] = t.d2[q];
+    for (int q = threadIdx.x; q < t.P; q += blockDim.x) sig[q] = t.sig[q];
+    if (threadIdx.x == 0) *status = 0;
+}
 
 // Device address of the scratch array on the current device (looked up once).
 cudaError_t scratch_address(void** out) {
@@ -81,20 +97,21 @@ extern "C" int dog_prune_noalloc(const dog_blob* d_cand, const int32_t* d_count,
 
     // conflict table and cell size, on the host (same rule as dog_create)
     const int P = n_planes;
-    int table[MAX_LEVELS * MAX_LEVELS];
+    NoallocTables t;
     int maxd2 = 1;
-    for (int a = 0; a < P; ++a)
+    for (int a = 0; a < P; ++a) {
+        t.sig[a] = h_sigmas[a];
         for (int q = 0; q < P; ++q) {
-            table[a * P + q] = conflict_d2(h_sigmas[a], h_sigmas[q], overlap);
-            if (table[a * P + q] > maxd2) maxd2 = table[a * P + q];
+            t.d2[a * P + q] = conflict_d2(h_sigmas[a], h_sigmas[q], overlap);
+            if (t.d2[a * P + q] > maxd2) maxd2 = t.d2[a * P + q];
         }
+    }
+    t.P = P;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the array keeps the last call's contents: the tables and the status
-    // word are rewritten here; the kernel initialises the per-candidate state
-    if (cudaMemcpyAsync(d2thr, table, sizeof(int) * P * P, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(sig, h_sigmas, sizeof(double) * P, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess)
-        return DOG_ERR_CUDA;
+    // the array keeps the last call's contents: the tables and the status word
+    // are rewritten here; the pruning kernel initialises the per-candidate state
+    noalloc_setup_kernel<<<1, 256, 0, s>>>(t, d2thr, sig, status);
+    if (cudaGetLastError() != cudaSuccess) return DOG_ERR_CUDA;
     PruneParams q{};
     q.cand = d_cand;
     q.cand_count = d_count;

@@ -20,6 +20,8 @@
 // largest conflict distance, so all conflicts lie in the 3x3 adjacent cells.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "dog_internal.cuh"
 
 namespace dogk {
@@ -315,16 +317,19 @@ __global__ void __launch_bounds__(PRUNE_THREADS) dog_prune_kernel(const __grid_c
     if (p.hist.hist) frame_hist(p, s, out, f);
 }
 
-static bool g_prune_attr[64];
+// Set once per device (not on every launch, so launches can be graph-captured);
+// atomic because the launcher may be called from several host threads.
+static std::atomic<bool> g_prune_attr[64];
 
 cudaError_t launch_prune(const PruneParams& p, cudaStream_t s) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (!g_prune_attr[dev & 63]) {   // once per device, so launches can be graph-captured
+    if (!g_prune_attr[dev & 63].load(std::memory_order_acquire)) {
+        // setting the attribute twice from two threads is harmless
         e = cudaFuncSetAttribute(dog_prune_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PRUNE_DYN_BYTES);
         if (e != cudaSuccess) return e;
-        g_prune_attr[dev & 63] = true;
+        g_prune_attr[dev & 63].store(true, std::memory_order_release);
     }
     dog_prune_kernel<<<p.n_frames, PRUNE_THREADS, PRUNE_DYN_BYTES, s>>>(p);
     return cudaGetLastError();

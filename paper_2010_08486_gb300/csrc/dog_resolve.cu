@@ -3,6 +3,8 @@
 // 32-column strip (Sec. 4: the maximum test over x, y and scale).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "dog_internal.cuh"
 #include "dog_device.cuh"
 
@@ -175,7 +177,8 @@ __global__ void __launch_bounds__(RES_THREADS) dog_resolve_kernel(const __grid_c
     }
 }
 
-static int g_resolve_smem[64];
+// Raised once per device; atomic because several host threads may launch.
+static std::atomic<int> g_resolve_smem[64];
 
 cudaError_t launch_resolve(const ResolveParams& p, int max_pending, cudaStream_t s) {
     int R = 0;
@@ -184,10 +187,13 @@ cudaError_t launch_resolve(const ResolveParams& p, int max_pending, cudaStream_t
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (smem > 48 * 1024 && g_resolve_smem[dev & 63] < smem) {
+    std::atomic<int>& lim = g_resolve_smem[dev & 63];
+    if (smem > 48 * 1024 && lim.load(std::memory_order_acquire) < smem) {
         e = cudaFuncSetAttribute(dog_resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        g_resolve_smem[dev & 63] = smem;
+        int cur = lim.load(std::memory_order_relaxed);
+        while (cur < smem && !lim.compare_exchange_weak(cur, smem)) {
+        }
     }
     int grid = max_pending;
     if (grid < 1) grid = 1;

@@ -1,8 +1,8 @@
 """dog_prune_noalloc: pruning for callers that may not allocate device memory
-(for example a plug-in whose host framework owns all device memory, or code
-recorded between stream-capture calls).  It must return what dog_prune
-returns for the same candidates, on consecutive calls that reuse its fixed
-internal scratch array.  This file is collected last on purpose."""
+(for example a plug-in whose host framework owns all device memory and
+forbids allocations inside its execution step).  It must return what
+dog_prune returns for the same candidates, on consecutive calls that reuse
+its fixed internal scratch array.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
