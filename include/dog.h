@@ -88,6 +88,12 @@ enum { DOG_DTYPE_F32 = 0, DOG_DTYPE_U16 = 1 };
  *  soft_T     temperature of the soft (sigmoid) threshold, differentiable form.
  *  max_h/max_w  largest frame a call will pass (sizes workspace).
  *  blob_cap   candidate capacity per frame held in the workspace.
+ *  stretch_sat  contrast stretch of 12-bit frames (Sec. 4, the optional
+ *             preprocessing step; the paper uses 0.0035): 0 = off.  When set,
+ *             every DOG_DTYPE_U16 frame a detection call ingests is mapped to
+ *             [0, 1] with its own limits as in dog_stretch_limits/dog_stretch
+ *             (computed on the device before the detection kernel, applied as
+ *             the kernel loads the counts); FP32 frames are used as given.
  */
 typedef struct dog_config {
     int32_t n_levels;
@@ -100,6 +106,7 @@ typedef struct dog_config {
     double soft_T;
     int32_t max_h, max_w;
     int32_t blob_cap;
+    double stretch_sat;
 } dog_config;
 
 /* One blob: centre (x, y), DoG plane, sigma (the plane's sigma, or the mean
@@ -123,7 +130,7 @@ typedef struct dog_handle dog_t;
 
 /* Fill *cfg with the defaults: GEOM ladder 1.0 .. 10.0 ratio 1.6, truncate
  * 4, threshold 0.1, overlap 0.5, DERIV, COALESCE, 32 LOGV bins, soft_T 0.01,
- * max frame 1024x1024, blob_cap 65536. */
+ * max frame 1024x1024, blob_cap 65536, no contrast stretch. */
 int dog_config_default(dog_config* cfg);
 
 /* Build a detector on the current CUDA device: computes the ladder, radii,
@@ -192,6 +199,25 @@ int dog_prune(dog_t* h, const dog_blob* d_cand, const int32_t* d_count, int32_t 
 int dog_prune_noalloc(const dog_blob* d_cand, const int32_t* d_count, int32_t cap_in,
                       const double* h_sigmas, int32_t n_planes, double overlap, int32_t mode,
                       dog_blob* d_out, int32_t cap_out, int32_t* d_nout, void* stream);
+
+/* Contrast-stretch limits of one frame of 12-bit counts (Sec. 4: the optional
+ * preprocessing step stretches a frame to [0, 1] with a saturation of 0.35%).
+ * With the n = img_h * img_w counts sorted ascending (counts above 4095 count
+ * as 4095) and k = floor(sat / 2 * n) (at most (n-1)/2), d_lohi[0] receives
+ * the count at rank k and d_lohi[1] the count at rank n-1-k (device, two
+ * int32).  d_hist is caller-owned device scratch of 4096 int32 (overwritten).
+ * sat in [0, 1); frames of 2^31 pixels or more are not supported.  No
+ * allocation; stream-ordered. */
+int dog_stretch_limits(const uint16_t* d_img, int32_t img_h, int32_t img_w, int32_t pitch, double sat,
+                       int32_t* d_hist, int32_t* d_lohi, void* stream);
+
+/* The stretched frame: d_out[y * out_pitch + x] = clamp((c - lo) / (hi - lo),
+ * 0, 1) for the count c (4095 at most) of pixel (x, y), as one IEEE single
+ * division of the two exact integers; lo = d_lohi[0], hi = d_lohi[1] (device);
+ * when hi == lo the result is 0 for c <= lo and 1 above.  FP32 output,
+ * row-major, pitch in elements. */
+int dog_stretch(const uint16_t* d_img, int32_t img_h, int32_t img_w, int32_t pitch, const int32_t* d_lohi,
+                float* d_out, int32_t out_pitch, void* stream);
 
 /* Blob-volume histogram (Sec. 4, Sec. 4.1: the pruned blobs are binned by volume).
  * d_hist: uint32 counts (nbins, or K-1 in LADDER mode), overwritten.
@@ -314,6 +340,15 @@ int dog_fma_peak(int32_t pair, int64_t iters, int32_t reps, double* h_tflops, do
 /* Read and clear the handle's device status word (synchronises the stream
  * passed to the last call).  *h_status receives DOG_OK or the first error. */
 int dog_get_status(dog_t* h, int32_t* h_status);
+
+/* Testing: make the library's device workspace allocations (dog_create and
+ * the growth of the batched workspace) fail on purpose.  After this call the
+ * next `after` such allocations succeed and the one following them reports
+ * out of memory without calling the CUDA allocator, so the caller sees
+ * DOG_ERR_NOMEM and the library frees what it had allocated; later ones succeed
+ * again.  -1 switches the injection off.  Process-wide; no counterpart in the
+ * paper. */
+int dog_test_fail_alloc(int32_t after);
 
 /* Human-readable name of a status code (static string). */
 const char* dog_status_string(int status);

@@ -31,10 +31,10 @@ NOALLOC_MAX_CAND = 65536
 # Every function declared in include/dog.h, in declaration order.
 EXPORTS = (
     "dog_config_default", "dog_create", "dog_destroy", "dog_ladder", "dog_candidates", "dog_prune",
-    "dog_prune_noalloc", "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_soft_hist",
+    "dog_prune_noalloc", "dog_stretch_limits", "dog_stretch", "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_soft_hist",
     "dog_backward", "dog_soft_hist_rec", "dog_backward_rec", "dog_debug_dog", "dog_ring_hist_push", "dog_ring_hist_push_batched",
     "dog_profile_enable", "dog_profile_read", "dog_fma_peak",
-    "dog_get_status", "dog_status_string",
+    "dog_get_status", "dog_test_fail_alloc", "dog_status_string",
 )
 
 
@@ -57,6 +57,7 @@ class DogConfig(ctypes.Structure):
         ("max_h", ctypes.c_int32),
         ("max_w", ctypes.c_int32),
         ("blob_cap", ctypes.c_int32),
+        ("stretch_sat", ctypes.c_double),
     ]
 
 
@@ -115,6 +116,8 @@ def load(path: str | None = None):
         lib.dog_prune.argtypes = [vp, vp, vp, i32, i32, i32, vp, i32, vp, vp]
         lib.dog_prune_noalloc.argtypes = [vp, vp, i32, P(ctypes.c_double), i32, ctypes.c_double, i32, vp, i32,
                                           vp, vp]
+        lib.dog_stretch_limits.argtypes = [vp, i32, i32, i32, ctypes.c_double, vp, vp, vp]
+        lib.dog_stretch.argtypes = [vp, i32, i32, i32, vp, vp, i32, vp]
         lib.dog_volume_hist.argtypes = [vp, vp, vp, i32, vp, vp, vp]
         lib.dog_detect.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp, vp, vp, vp]
         lib.dog_detect_batched.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp]
@@ -130,6 +133,7 @@ def load(path: str | None = None):
         lib.dog_profile_read.argtypes = [vp, P(ctypes.c_double), P(i32)]
         lib.dog_fma_peak.argtypes = [i32, ctypes.c_int64, i32, P(ctypes.c_double), P(ctypes.c_double), vp]
         lib.dog_get_status.argtypes = [vp, P(i32)]
+        lib.dog_test_fail_alloc.argtypes = [i32]
         lib.dog_status_string.argtypes = [ctypes.c_int]
         lib.dog_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -86,6 +87,12 @@ struct dog_handle {
     int* d_bcounts = nullptr;
     Pending* d_bpend = nullptr;
     int bpend_cap = 0;
+    // contrast stretch: histogram and limits of a single frame, and of each
+    // frame of a batch (grown with the batch workspace)
+    int* d_shist = nullptr;
+    int* d_slohi = nullptr;
+    int* d_bshist = nullptr;
+    int* d_bslohi = nullptr;
     // differentiable form
     void* soft_ws = nullptr;
     cudaStream_t last = nullptr;
@@ -181,8 +188,19 @@ static int status_from(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? DOG_ERR_NOMEM : DOG_ERR_CUDA;
 }
 
+// Allocation failures injected by dog_test_fail_alloc: the number of
+// workspace allocations still allowed before one fails (-1: none fails).
+static std::atomic<int> g_fail_after{-1};
+
 template <class T>
 static cudaError_t dalloc(T** p, size_t n) {
+    int k = g_fail_after.load();
+    while (k >= 0 && !g_fail_after.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0) {   // this allocation is the injected failure; later ones succeed again
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(n, 1));
 }
 
@@ -190,7 +208,8 @@ static void free_all(dog_handle* h) {
     void* ptrs[] = {h->d_w, h->d_c, h->d_sig64, h->d_d2thr, h->d_sigf, h->d_levbin, h->d_logsig,
                     h->d_cand, h->d_counts, h->d_pend, h->d_state, h->d_target, h->d_order,
                     h->d_status, h->d_desc, h->d_cand_off, h->d_out_off, h->d_hw, h->d_ntiles,
-                    h->d_bcand, h->d_bstate, h->d_btarget, h->d_border, h->d_bcounts, h->d_bpend};
+                    h->d_bcand, h->d_bstate, h->d_btarget, h->d_border, h->d_bcounts, h->d_bpend,
+                    h->d_shist, h->d_slohi, h->d_bshist, h->d_bslohi};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -238,6 +257,7 @@ int dog_config_default(dog_config* c) {
     c->max_h = 1024;
     c->max_w = 1024;
     c->blob_cap = 65536;
+    c->stretch_sat = 0.0;
     return DOG_OK;
 }
 
@@ -247,7 +267,7 @@ int dog_create(const dog_config* cfg, dog_t** out) {
     const dog_config& c = *cfg;
     if (!(c.truncate > 0.0) || !(c.overlap >= 0.0 && c.overlap < 1.0) || c.nbins < 1 ||
         c.nbins > DOG_MAX_NBINS || c.max_h < 1 || c.max_w < 1 || c.blob_cap < 1 ||
-        !(c.soft_T > 0.0))
+        !(c.soft_T > 0.0) || !(c.stretch_sat >= 0.0 && c.stretch_sat < 1.0))
         return DOG_ERR_INVALID;
     if (c.norm != DOG_NORM_DERIV && c.norm != DOG_NORM_PAPER) return DOG_ERR_INVALID;
     if (c.prune < DOG_PRUNE_COALESCE || c.prune > DOG_PRUNE_OFF) return DOG_ERR_INVALID;
@@ -433,6 +453,8 @@ int dog_create(const dog_config* cfg, dog_t** out) {
     ok(dalloc(&h->d_target, h->cand_cap));
     ok(dalloc(&h->d_order, h->cand_cap));
     ok(dalloc(&h->d_status, 1));
+    ok(dalloc(&h->d_shist, STRETCH_BINS));
+    ok(dalloc(&h->d_slohi, 2));
     if (e == cudaSuccess) {
         ok(cudaMemcpy(h->d_w, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice));
         ok(cudaMemcpy(h->d_c, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice));
@@ -485,18 +507,31 @@ int dog_set_tiling(dog_t* h, int32_t band_rows, int32_t ctas_per_sm) {
     return DOG_OK;
 }
 
+// The contrast stretch applies to 12-bit frames when the handle's stretch_sat
+// is set (frames of more than 2^31 pixels are not supported then).
+static bool stretches(const dog_handle* h, int dtype) {
+    return h->cfg.stretch_sat > 0.0 && dtype == DOG_DTYPE_U16;
+}
+
 static int check_frame(const dog_handle* h, const void* img, int dtype, int H, int W, int pitch) {
     if (!img || H < 1 || W < 1 || pitch < W) return DOG_ERR_INVALID;
     if (dtype != DOG_DTYPE_F32 && dtype != DOG_DTYPE_U16) return DOG_ERR_INVALID;
     if (H > 65535 || W > 65535) return DOG_ERR_UNSUPPORTED;
-    (void)h;
+    if (stretches(h, dtype) && (long long)H * W >= (1LL << 31)) return DOG_ERR_UNSUPPORTED;
     return DOG_OK;
+}
+
+// Limits of a single 12-bit frame into the handle's workspace.
+static cudaError_t single_limits(dog_handle* h, const void* img, int H, int W, int pitch, cudaStream_t s) {
+    return launch_stretch_limits(nullptr, 1, static_cast<const uint16_t*>(img), H, W, pitch, h->cfg.stretch_sat,
+                                 h->num_sms, h->d_shist, h->d_slohi, s);
 }
 
 static FusedParams frame_params(const dog_handle* h, const void* img, int dtype, int H, int W, int pitch) {
     FusedParams p = h->base;
     p.img = img;
-    p.dtype = dtype;
+    p.dtype = stretches(h, dtype) ? DTYPE_U16_STRETCH : dtype;
+    p.lohi = h->d_slohi;
     p.H = H;
     p.W = W;
     p.pitch = pitch;
@@ -515,6 +550,7 @@ static ResolveParams resolve_params(const dog_handle* h, const FusedParams& f) {
     r.frames = nullptr;
     r.img = f.img;
     r.dtype = f.dtype;
+    r.lohi = f.lohi;
     r.H = f.H;
     r.W = f.W;
     r.pitch = f.pitch;
@@ -561,6 +597,7 @@ int dog_candidates(dog_t* h, const void* d_img, int32_t dtype, int32_t H, int32_
     p.pend_count = h->d_counts + 1;
     DOG_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
     DOG_CUDA(cudaMemsetAsync(h->d_counts + 1, 0, sizeof(int), s));
+    if (p.dtype == DTYPE_U16_STRETCH) DOG_CUDA(single_limits(h, d_img, H, W, pitch, s));
     DOG_CUDA(timed_fused(h, p, p.n_strips * p.n_bands, s));
     ResolveParams r = resolve_params(h, p);
     DOG_CUDA(launch_resolve(r, h->pend_cap, s));
@@ -577,6 +614,7 @@ int dog_debug_dog(dog_t* h, const void* d_img, int32_t dtype, int32_t H, int32_t
     FusedParams p = frame_params(h, d_img, dtype, H, W, pitch);
     p.mode = MODE_DUMP;
     p.dump = d_dog;
+    if (p.dtype == DTYPE_U16_STRETCH) DOG_CUDA(single_limits(h, d_img, H, W, pitch, s));
     DOG_CUDA(timed_fused(h, p, p.n_strips * p.n_bands, s));
     return DOG_OK;
 }
@@ -687,12 +725,13 @@ static int grow_batch(dog_handle* h, int n) {
     if (n <= h->batch_cap) return DOG_OK;
     cudaDeviceSynchronize();
     void* olds[] = {h->d_desc, h->d_cand_off, h->d_out_off, h->d_hw, h->d_ntiles, h->d_bcand,
-                    h->d_bstate, h->d_btarget, h->d_border, h->d_bcounts, h->d_bpend};
+                    h->d_bstate, h->d_btarget, h->d_border, h->d_bcounts, h->d_bpend, h->d_bshist, h->d_bslohi};
     for (void* p : olds)
         if (p) cudaFree(p);
     h->d_desc = nullptr; h->d_cand_off = nullptr; h->d_out_off = nullptr; h->d_hw = nullptr;
     h->d_ntiles = nullptr; h->d_bcand = nullptr; h->d_bstate = nullptr; h->d_btarget = nullptr;
-    h->d_border = nullptr; h->d_bcounts = nullptr; h->d_bpend = nullptr;
+    h->d_border = nullptr; h->d_bcounts = nullptr; h->d_bpend = nullptr; h->d_bshist = nullptr;
+    h->d_bslohi = nullptr;
     h->batch_cap = 0;
     const size_t nc = (size_t)n * h->cand_cap;
     cudaError_t e = cudaSuccess;
@@ -709,6 +748,8 @@ static int grow_batch(dog_handle* h, int n) {
     ok(dalloc(&h->d_bcounts, n + 4));
     h->bpend_cap = (int)std::min<size_t>(nc, (size_t)1 << 26);
     ok(dalloc(&h->d_bpend, h->bpend_cap));
+    ok(dalloc(&h->d_bshist, (size_t)n * STRETCH_BINS));
+    ok(dalloc(&h->d_bslohi, 2 * (size_t)n));
     if (e == cudaSuccess) ok(cudaMemset(h->d_bcounts, 0, sizeof(int) * (n + 4)));
     if (e != cudaSuccess) return status_from(e);
     h->batch_cap = n;
@@ -718,6 +759,8 @@ static int grow_batch(dog_handle* h, int n) {
 int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t max_h, int32_t max_w,
                        dog_blob* d_blobs, int32_t* d_counts, uint32_t* d_hists, void* stream) {
     if (!h || !d_frames || n < 1 || !d_blobs || !d_counts || max_h < 1 || max_w < 1) return DOG_ERR_INVALID;
+    const bool stretch = h->cfg.stretch_sat > 0.0;
+    if (stretch && (long long)max_h * max_w >= (1LL << 31)) return DOG_ERR_UNSUPPORTED;
     int st = grow_batch(h, n);
     if (st != DOG_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -725,8 +768,12 @@ int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t m
     const int band = (h->band > 0) ? h->band : 0;
     // per-frame descriptors, candidate/output offsets and the tile prefix sum
     const int grid = h->num_sms * h->ctas_per_sm;
-    DOG_CUDA(launch_batch_prep(d_frames, n, band, grid, h->cand_cap, h->d_desc, h->d_cand_off, h->d_out_off,
-                               h->d_hw, h->d_ntiles, s));
+    // contrast-stretch limits of the batch's 12-bit frames
+    if (stretch)
+        DOG_CUDA(launch_stretch_limits(d_frames, n, nullptr, 0, 0, 0, h->cfg.stretch_sat, h->num_sms, h->d_bshist,
+                                       h->d_bslohi, s));
+    DOG_CUDA(launch_batch_prep(d_frames, n, band, grid, h->cand_cap, stretch, h->d_desc, h->d_cand_off,
+                               h->d_out_off, h->d_hw, h->d_ntiles, s));
     // fixed slots: the persistent kernel's work and completion counters are
     // zero between launches (the last CTA resets them), whatever n was
     int* tile_counter = h->d_bcounts + 0;
@@ -749,6 +796,7 @@ int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t m
     p.pend_cap = h->bpend_cap;
     p.pend_count = pend_count;
     p.ntiles_dev = h->d_ntiles;
+    p.lohi = h->d_bslohi;
     DOG_CUDA(timed_fused(h, p, grid, s));
     ResolveParams r = resolve_params(h, p);
     r.frames = h->d_desc;
@@ -867,6 +915,12 @@ int dog_get_status(dog_t* h, int32_t* h_status) {
     if (cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DOG_ERR_CUDA;
     if (cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) return DOG_ERR_CUDA;
     *h_status = v;
+    return DOG_OK;
+}
+
+int dog_test_fail_alloc(int32_t after) {
+    if (after < -1) return DOG_ERR_INVALID;
+    g_fail_after.store(after);
     return DOG_OK;
 }
 

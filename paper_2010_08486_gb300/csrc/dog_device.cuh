@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "dog.h"
+#include "dog_internal.cuh"
 
 namespace dogk {
 
@@ -19,15 +20,28 @@ __device__ __forceinline__ int refl(int i, int n) {
     return m >= n ? p - 1 - m : m;
 }
 
+// Contrast stretch of one count (Sec. 4 preprocessing): counts above 4095 act
+// as 4095; (c - lo) / (hi - lo) by one IEEE single division (both operands
+// are exact integers), clipped to [0, 1]; equal limits map to 0 at or below
+// the limit and 1 above.
+__device__ __forceinline__ float stretch_px(unsigned v, int lo, int hi) {
+    const int c = min((int)v, STRETCH_BINS - 1);
+    if (hi <= lo) return c > lo ? 1.0f : 0.0f;
+    const float t = __fdiv_rn((float)(c - lo), (float)(hi - lo));
+    return fminf(fmaxf(t, 0.0f), 1.0f);
+}
+
 // Raw pixel load and its conversion to [0, 1] (uint16 counts: one IEEE
-// division by 4095).
+// division by 4095, or the contrast stretch with limits lo, hi).
 __device__ __forceinline__ unsigned load_raw(const void* img, int dtype, int pitch, int y, int x) {
-    if (dtype == DOG_DTYPE_U16)
+    if (dtype != DOG_DTYPE_F32)
         return (unsigned)__ldg(reinterpret_cast<const unsigned short*>(img) + (size_t)y * pitch + x);
     return __float_as_uint(__ldg(reinterpret_cast<const float*>(img) + (size_t)y * pitch + x));
 }
-__device__ __forceinline__ float raw_to_px(unsigned v, int dtype) {
-    return dtype == DOG_DTYPE_U16 ? __fdiv_rn((float)v, 4095.0f) : __uint_as_float(v);
+__device__ __forceinline__ float raw_to_px(unsigned v, int dtype, int lo, int hi) {
+    if (dtype == DOG_DTYPE_U16) return __fdiv_rn((float)v, 4095.0f);
+    if (dtype == DTYPE_U16_STRETCH) return stretch_px(v, lo, hi);
+    return __uint_as_float(v);
 }
 
 __device__ __forceinline__ float dog_value(float c, float a, float b) {

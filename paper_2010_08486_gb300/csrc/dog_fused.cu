@@ -114,6 +114,7 @@ __device__ __forceinline__ void vpass(const float* __restrict__ ring, int lane, 
 struct TileCtx {
     const void* img;
     int dtype, H, W, pitch;
+    int st_lo, st_hi;   // contrast-stretch limits (DTYPE_U16_STRETCH)
     int frame;
     int x0, y0, y1;
     dog_blob* blobs;
@@ -237,7 +238,7 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
 #pragma unroll
             for (int k = 0; k < NPF; ++k) {
                 const int cc = lane + 32 * k;
-                if (cc < ncols) dst[cc] = raw_to_px(pf[k], tc.dtype);
+                if (cc < ncols) dst[cc] = raw_to_px(pf[k], tc.dtype, tc.st_lo, tc.st_hi);
             }
         }
         if (b >= 0) bar_arrive(BAR_FULL + (b & 1), NTHREADS);
@@ -552,7 +553,8 @@ __device__ __forceinline__ void process_tile(const FusedParams& p, float* sm, Sm
                 const int i = i0 + u * NTHREADS + tid;
                 if (i < total) {
                     const int rr = i / ncols, cc = i - rr * ncols;
-                    in[((y0 + rr - yorg) & (p.in_rows - 1)) * p.in_stride + cc] = raw_to_px(v[u], tc.dtype);
+                    in[((y0 + rr - yorg) & (p.in_rows - 1)) * p.in_stride + cc] =
+                        raw_to_px(v[u], tc.dtype, tc.st_lo, tc.st_hi);
                 }
             }
         }
@@ -611,6 +613,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
         __syncthreads();
         TileCtx tc;
         tc.img = p.img; tc.dtype = p.dtype; tc.H = p.H; tc.W = p.W; tc.pitch = p.pitch; tc.frame = 0;
+        tc.st_lo = tc.dtype == DTYPE_U16_STRETCH ? p.lohi[0] : 0;
+        tc.st_hi = tc.dtype == DTYPE_U16_STRETCH ? p.lohi[1] : 0;
         const int strip = blockIdx.x % p.n_strips;
         const int band = blockIdx.x / p.n_strips;
         tc.x0 = strip * TX;
@@ -637,6 +641,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) dog_fused_kernel(const __grid_con
             const int local = (int)(t - f.tile_begin);
             TileCtx tc;
             tc.img = f.img; tc.dtype = f.dtype; tc.H = f.h; tc.W = f.w; tc.pitch = f.pitch; tc.frame = lo;
+            tc.st_lo = tc.dtype == DTYPE_U16_STRETCH ? p.lohi[2 * lo] : 0;
+            tc.st_hi = tc.dtype == DTYPE_U16_STRETCH ? p.lohi[2 * lo + 1] : 0;
             tc.x0 = (local % f.n_strips) * TX;
             const int band = local / f.n_strips;
             const int bh = f.band;
@@ -754,7 +760,8 @@ __device__ __forceinline__ long long block_scan(long long v, long long* wsum, lo
 }
 
 __global__ void __launch_bounds__(1024) dog_batch_prep_kernel(const dog_frame* frames, int n, int band,
-                                                              int tail_tiles, int blob_cap, FrameDesc* desc,
+                                                              int tail_tiles, int blob_cap, bool stretch,
+                                                              FrameDesc* desc,
                                                               long long* cand_off, long long* out_off,
                                                               int* hw, long long* ntiles) {
     __shared__ long long carry, total;
@@ -772,7 +779,7 @@ __global__ void __launch_bounds__(1024) dog_batch_prep_kernel(const dog_frame* f
             d.h = fr.h;
             d.w = fr.w;
             d.pitch = fr.pitch;
-            d.dtype = fr.dtype;
+            d.dtype = (stretch && fr.dtype == DOG_DTYPE_U16) ? DTYPE_U16_STRETCH : fr.dtype;
             d.blob_off = (long long)f * blob_cap;
             d.n_strips = (fr.w + TX - 1) / TX;
             d.band = (band > 0 && band < fr.h) ? band : fr.h;
@@ -816,10 +823,10 @@ __global__ void __launch_bounds__(1024) dog_batch_prep_kernel(const dog_frame* f
 }
 
 cudaError_t launch_batch_prep(const dog_frame* frames, int n, int band, int tail_tiles, int blob_cap,
-                              FrameDesc* desc, long long* cand_off, long long* out_off, int* hw, long long* ntiles,
-                              cudaStream_t s) {
-    dog_batch_prep_kernel<<<1, 1024, 0, s>>>(frames, n, band, tail_tiles, blob_cap, desc, cand_off, out_off, hw,
-                                             ntiles);
+                              bool stretch, FrameDesc* desc, long long* cand_off, long long* out_off, int* hw,
+                              long long* ntiles, cudaStream_t s) {
+    dog_batch_prep_kernel<<<1, 1024, 0, s>>>(frames, n, band, tail_tiles, blob_cap, stretch, desc, cand_off,
+                                             out_off, hw, ntiles);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,11 @@ constexpr int MAX_LEVELS = DOG_MAX_LEVELS;
 static_assert(MB % NCONS == 0, "each consumer warp tests whole rows of a block");
 static_assert(NTHREADS <= 1024, "one CTA");
 
+// Internal pixel type: 12-bit counts contrast stretched with per-frame limits
+// (the public types are DOG_DTYPE_F32 and DOG_DTYPE_U16).
+constexpr int DTYPE_U16_STRETCH = 2;
+constexpr int STRETCH_BINS = 4096;   // histogram bins of the 12-bit counts
+
 enum FusedMode : int {
     MODE_CANDIDATES = 0,  // thresholded maxima -> blob list (+ pending strip-edge list)
     MODE_DUMP = 1,        // write D for every voxel
@@ -64,6 +69,7 @@ struct FusedParams {
     // single-frame mode (batched mode reads FrameDesc instead)
     const void* img;
     int dtype, H, W, pitch;
+    const int* lohi;       // contrast-stretch limits (lo, hi) per frame (DTYPE_U16_STRETCH frames)
     int band;              // output rows per CTA (multiple of MB)
     int n_strips, n_bands;
     // batched mode
@@ -119,6 +125,7 @@ struct ResolveParams {
     const FrameDesc* frames;  // batched: per-frame image; single: frames == nullptr
     const void* img;
     int dtype, H, W, pitch;
+    const int* lohi;          // contrast-stretch limits per frame (as FusedParams)
     int K, P;
     const float* w;
     const float* c;
@@ -148,8 +155,15 @@ struct ResolveParams {
 cudaError_t launch_fused(const FusedParams& p, int grid, cudaStream_t s);
 cudaError_t launch_resolve(const ResolveParams& p, int max_pending, cudaStream_t s);
 cudaError_t launch_batch_prep(const dog_frame* frames, int n, int band, int tail_tiles, int blob_cap,
-                              FrameDesc* desc, long long* cand_off, long long* out_off, int* hw, long long* ntiles,
-                              cudaStream_t s);
+                              bool stretch, FrameDesc* desc, long long* cand_off, long long* out_off, int* hw,
+                              long long* ntiles, cudaStream_t s);
+// contrast stretch (dog_stretch.cu): per-frame histograms (STRETCH_BINS ints
+// per frame, zeroed here) and limits lohi (2 ints per frame) of the single
+// frame (frames == nullptr) or of the U16 frames of a device frame table
+cudaError_t launch_stretch_limits(const dog_frame* frames, int n, const uint16_t* img, int H, int W, int pitch,
+                                  double sat, int num_sms, int* hist, int* lohi, cudaStream_t s);
+cudaError_t launch_stretch_apply(const uint16_t* img, int H, int W, int pitch, const int* lohi, float* out,
+                                 int out_pitch, int num_sms, cudaStream_t s);
 
 struct HistParams {
     const dog_blob* blobs;

@@ -36,6 +36,7 @@ class DetectorConfig:
     max_h: int = 1024
     max_w: int = 1024
     blob_cap: int = 65536
+    stretch_sat: float = 0.0
 
     def to_c(self):
         c = _lib.DogConfig()
@@ -116,6 +117,32 @@ class BlobList:
 def empty_blobs(cap: int, device) -> BlobList:
     return BlobList(torch.empty((cap, 5), dtype=torch.int32, device=device),
                     torch.zeros((), dtype=torch.int32, device=device))
+
+
+def stretch_limits(counts: torch.Tensor, sat: float = 0.0035, stream=None) -> torch.Tensor:
+    """Contrast-stretch limits (lo, hi) of one frame of 12-bit counts (Sec. 4
+    preprocessing; dog_stretch_limits): a (2,) int32 device tensor."""
+    if _img_dtype(counts) != _lib.DTYPE_U16:
+        raise TypeError("the contrast stretch takes 16-bit counts")
+    H, W, pitch = _check_img(counts)
+    hist = torch.empty(4096, dtype=torch.int32, device=counts.device)
+    lohi = torch.empty(2, dtype=torch.int32, device=counts.device)
+    check(_lib.load().dog_stretch_limits(counts.data_ptr(), H, W, pitch, float(sat), hist.data_ptr(),
+                                         lohi.data_ptr(), _stream(stream)), "dog_stretch_limits")
+    return lohi
+
+
+def stretch(counts: torch.Tensor, lohi: torch.Tensor | None = None, sat: float = 0.0035,
+            stream=None) -> torch.Tensor:
+    """The stretched FP32 frame in [0, 1] (dog_stretch), with the frame's own
+    limits unless `lohi` is given."""
+    if lohi is None:
+        lohi = stretch_limits(counts, sat, stream)
+    H, W, pitch = _check_img(counts)
+    out = torch.empty((H, W), dtype=torch.float32, device=counts.device)
+    check(_lib.load().dog_stretch(counts.data_ptr(), H, W, pitch, lohi.data_ptr(), out.data_ptr(), W,
+                                  _stream(stream)), "dog_stretch")
+    return out
 
 
 class Detector:

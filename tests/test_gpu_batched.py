@@ -154,3 +154,39 @@ def test_bench_launch_configuration_matches_per_frame_and_oracle_histogram():
         np.testing.assert_array_equal(got[f][1], hist.cpu().numpy())
         want_counts, _ = oracle.hist(parity.blobs_to_oracle(x, y, l, s, r), p)
         np.testing.assert_array_equal(got[f][1], want_counts.astype(np.int32))
+
+
+def test_batched_workload_sizes_match_oracle():
+    """The batched and serving frame sizes checked against the FP64 oracle,
+    not only against the per-frame GPU path: one persistent launch over a
+    1024x1280, a 768x1024 and a 512x512 12-bit PLIF frame; per frame, the
+    decidable candidates of the same frame equal the oracle's (Sec. 4.1
+    threshold and 3x3x3 maximum), the batched pruned blobs equal the oracle's
+    coalescing of those candidates, and the histogram equals the oracle's."""
+    import oracle
+    from tests import parity
+    shapes = [(1024, 1280), (768, 1024), (512, 512)]
+    counts_np = [synth.plif_frame_u16(synth.BATCH_SEED_BASE + 40 + f, h, w) for f, (h, w) in enumerate(shapes)]
+    imgs = [torch.from_numpy(c.view(np.int16)).cuda() for c in counts_np]
+    cap = 16384
+    cfg = dog.plif_config(max_h=1024, max_w=1280, blob_cap=cap)
+    det = dog.Detector(cfg)
+    p = parity.oracle_params(cfg)
+    sig = oracle.ladder(p)
+    rad = oracle.radii(sig, p.truncate)
+    out, counts, hists = det.detect_batched(imgs)
+    torch.cuda.synchronize()
+    c = counts.cpu().numpy()
+    for f, (h, w) in enumerate(shapes):
+        img32 = synth.u16_to_f32(counts_np[f])
+        D_ora = oracle.dog(img32.astype(np.float64), sig, rad, p.norm)
+        cand = det.candidates(imgs[f])
+        torch.cuda.synchronize()
+        x, y, l, s, r = cand.to_numpy()
+        parity.compare_candidates(set(zip(l.tolist(), y.tolist(), x.tolist())), D_ora, cfg.threshold)
+        ora_pr = oracle.prune(parity.blobs_to_oracle(x, y, l, s, r), p)
+        ora_pr.sigma = ora_pr.sigma.astype(np.float32).astype(np.float64)
+        got = parity.blobs_to_oracle(*dog.blobs_from_raw(out[f * cap:(f + 1) * cap], int(c[f])))
+        assert parity.same_blob_sets(got, ora_pr), "frame %dx%d: batched blobs differ from the oracle" % (h, w)
+        np.testing.assert_array_equal(hists[f].cpu().numpy(), oracle.hist(got, p)[0].astype(np.int32))
+    assert det.status() == 0
