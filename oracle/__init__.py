@@ -69,6 +69,11 @@ def _load():
         lib.ora_stretch_limits.argtypes = [u16p, ctypes.c_long, d, i32p, i32p]
         lib.ora_stretch_limits.restype = i
         lib.ora_stretch.argtypes = [u16p, ctypes.c_long, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_float)]
+        u32p = P(ctypes.c_uint32)
+        lib.ora_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        lib.ora_render_spheres.argtypes = [P(ctypes.c_float), i, i, i, i, ctypes.c_float, d, d, ctypes.c_uint64,
+                                           P(ctypes.c_float), u16p]
+        lib.ora_render_spheres.restype = i
         lib.ora_num_threads.restype = i
         lib.ora_reflect.argtypes = [ctypes.c_long, ctypes.c_long]
         lib.ora_reflect.restype = ctypes.c_long
@@ -461,3 +466,33 @@ def preprocess(counts, sat: float = 0.0035) -> np.ndarray:
     """Contrast-stretched frame with the frame's own limits."""
     lo, hi = stretch_limits(counts, sat)
     return stretch(counts, lo, hi)
+
+
+# ---------------------------------------------------------------------------
+# Synthetic sphere frames (Sec. 5: 100 rendered spheres with Poisson and
+# Gaussian noise); the shading reading is stated in dog_oracle.c.
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block (Salmon et al., SC'11) of a 4-word counter and a
+    2-word key."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xffffffff for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xffffffff for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    _load().ora_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def render_spheres(spheres, h: int, w: int, ss: int = 4, background: float = 0.05, gain: float = 2000.0,
+                   read_noise: float = 4.0, seed: int = 0):
+    """(intensity (h, w) float32, counts (h, w) uint16) of a sphere table
+    (S, 4): cx, cy, R, A."""
+    sp = np.ascontiguousarray(spheres, dtype=np.float32).reshape(-1, 4)
+    inten = np.empty((h, w), dtype=np.float32)
+    counts = np.empty((h, w), dtype=np.uint16)
+    rc = _load().ora_render_spheres(sp.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), sp.shape[0], h, w, ss,
+                                    float(background), float(gain), float(read_noise), int(seed),
+                                    inten.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                    counts.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)))
+    if rc != 0:
+        raise ValueError("render_spheres failed (%d)" % rc)
+    return inten, counts

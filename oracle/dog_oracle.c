@@ -603,3 +603,92 @@ void ora_stretch(const uint16_t* c, long n, int32_t lo, int32_t hi, float* out) 
         out[i] = (float)t;
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Synthetic sphere frames (Sec. 5 evaluates on frames of 100 rendered spheres
+ * with Poisson and Gaussian noise; the paper names no shading model).
+ * Reading: each sphere is an optically thin fluorescent droplet, so a
+ * pixel's brightness is proportional to the chord length through the sphere
+ * along the viewing axis, sqrt(1 - d^2 / R^2) at distance d from the centre,
+ * averaged over ss x ss sub-pixel samples; the frame is a background plus the
+ * spheres' contributions in table order, all in IEEE single precision with
+ * the operations in the order written.  Counts are
+ *   floor(lambda + sqrt(lambda) z1 + read_noise z2 + 1/2) clipped to [0, 4095],
+ *   lambda = gain * intensity
+ * (shot noise as a Gaussian of variance lambda, the large-count form of the
+ * Poisson law, plus Gaussian read noise), in double.  z1 and z2 are sums of
+ * twelve uniforms minus 6, the uniforms being the top 24 bits of Philox4x32-10
+ * outputs (Salmon et al., SC'11) with counter (pixel index low, high, draw, 0)
+ * and key (seed low, high): three blocks per normal. */
+static void ora_mulhilo32(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo) {
+    const uint64_t p = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(p >> 32);
+    *lo = (uint32_t)p;
+}
+
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint32_t hi0, lo0, hi1, lo1;
+        ora_mulhilo32(0xD2511F53u, c0, &hi0, &lo0);
+        ora_mulhilo32(0xCD9E8D57u, c2, &hi1, &lo1);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static double ora_normal12(uint64_t pix, uint32_t draw0, const uint32_t key[2]) {
+    double s = 0.0;
+    for (uint32_t b = 0; b < 3; ++b) {
+        const uint32_t ctr[4] = {(uint32_t)pix, (uint32_t)(pix >> 32), draw0 + b, 0u};
+        uint32_t r[4];
+        ora_philox4x32_10(ctr, key, r);
+        for (int q = 0; q < 4; ++q) s += (double)(r[q] >> 8) * (1.0 / 16777216.0);
+    }
+    return s - 6.0;
+}
+
+/* spheres: S x 4 floats (cx, cy, R, A); intensity (H x W float, may be NULL),
+ * counts (H x W uint16).  ss in {1, 2, 4, 8}. */
+int ora_render_spheres(const float* spheres, int S, int H, int W, int ss, float background, double gain,
+                       double read_noise, uint64_t seed, float* intensity, uint16_t* counts) {
+    if (S < 0 || H < 1 || W < 1 || !(ss == 1 || ss == 2 || ss == 4 || ss == 8)) return -1;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const float inv_n = 1.0f / (float)(ss * ss);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            float I = background;
+            for (int s = 0; s < S; ++s) {
+                const float cx = spheres[4 * s], cy = spheres[4 * s + 1], R = spheres[4 * s + 2];
+                const float A = spheres[4 * s + 3];
+                const float inv_r2 = 1.0f / (R * R);
+                float acc = 0.0f;
+                for (int j = 0; j < ss; ++j) {
+                    const float v = (float)y + ((float)(2 * j + 1) / (float)(2 * ss) - 0.5f);
+                    const float dy = v - cy;
+                    for (int i = 0; i < ss; ++i) {
+                        const float u = (float)x + ((float)(2 * i + 1) / (float)(2 * ss) - 0.5f);
+                        const float dx = u - cx;
+                        const float q = 1.0f - (dx * dx + dy * dy) * inv_r2;
+                        if (q > 0.0f) acc = acc + sqrtf(q);
+                    }
+                }
+                I = I + A * (acc * inv_n);
+            }
+            if (intensity) intensity[(size_t)y * W + x] = I;
+            const uint64_t pix = (uint64_t)y * (uint64_t)W + (uint64_t)x;
+            const double lam = gain * (double)I;
+            const double z1 = ora_normal12(pix, 0u, key), z2 = ora_normal12(pix, 3u, key);
+            double n = floor(lam + sqrt(lam > 0.0 ? lam : 0.0) * z1 + read_noise * z2 + 0.5);
+            if (n < 0.0) n = 0.0;
+            if (n > 4095.0) n = 4095.0;
+            counts[(size_t)y * W + x] = (uint16_t)n;
+        }
+    }
+    return 0;
+}

@@ -145,3 +145,20 @@ def isolated_blob_frame(h: int, w: int, centres, s, amp) -> np.ndarray:
     _add_blobs(img, cx, cy, np.broadcast_to(np.asarray(s, dtype=np.float64), (len(cx),)),
                np.broadcast_to(np.asarray(amp, dtype=np.float64), (len(cx),)))
     return img
+
+
+SPHERE_SEED_BASE = 6_000_000
+
+
+def sphere_table(seed: int, n: int = 100, h: int = 1000, w: int = 1000, r_range=(3.0, 20.0),
+                 amp_range=(0.3, 1.0)) -> np.ndarray:
+    """(n, 4) float32 sphere table (cx, cy, R, A) for the rendered-sphere frames
+    of the paper's evaluation (100 spheres on 1000 x 1000 frames): centres
+    uniform over the frame, radii uniform in r_range (pixels), brightness
+    uniform in amp_range."""
+    g = _rng(seed)
+    cx = g.uniform(0, w, n)
+    cy = g.uniform(0, h, n)
+    r = g.uniform(r_range[0], r_range[1], n)
+    a = g.uniform(amp_range[0], amp_range[1], n)
+    return np.stack([cx, cy, r, a], axis=1).astype(np.float32)
