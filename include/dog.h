@@ -219,6 +219,28 @@ int dog_stretch_limits(const uint16_t* d_img, int32_t img_h, int32_t img_w, int3
 int dog_stretch(const uint16_t* d_img, int32_t img_h, int32_t img_w, int32_t pitch, const int32_t* d_lohi,
                 float* d_out, int32_t out_pitch, void* stream);
 
+/* Synthetic frame of rendered spheres (Sec. 5 evaluates on 1000 x 1000
+ * frames of 100 rendered spheres with Poisson and Gaussian noise; the paper
+ * names no shading model, so the one below is this library's reading).
+ *  d_spheres   n_spheres x 4 floats (cx, cy, R, A), device, 16-byte aligned;
+ *              at most 8192 spheres.
+ *  intensity   background + sum over spheres (table order) of
+ *              A * mean over ss x ss sub-pixel samples of sqrt(max(0, 1 -
+ *              d^2/R^2)) (chord length of an optically thin sphere), pixel
+ *              centres at integer coordinates, single precision with every
+ *              operation rounded as written; written to d_intensity (row
+ *              pitch img_w) unless it is NULL.  ss in {1, 2, 4, 8}.
+ *  counts      floor(lambda + sqrt(lambda) z1 + read_noise z2 + 1/2) clipped
+ *              to [0, 4095], lambda = gain * intensity, in double; z1, z2 are
+ *              sums of twelve uniforms minus 6, the uniforms being the top 24
+ *              bits of Philox4x32-10 blocks with counter (y * img_w + x low
+ *              and high word, draw, 0) and key (seed low, high), draws 0..2
+ *              for z1 and 3..5 for z2.  uint16, row pitch `pitch` elements.
+ * No allocation; stream-ordered. */
+int dog_render_spheres(const float* d_spheres, int32_t n_spheres, int32_t img_h, int32_t img_w, int32_t ss,
+                       float background, double gain, double read_noise, uint64_t seed, float* d_intensity,
+                       uint16_t* d_counts, int32_t pitch, void* stream);
+
 /* Blob-volume histogram (Sec. 4, Sec. 4.1: the pruned blobs are binned by volume).
  * d_hist: uint32 counts (nbins, or K-1 in LADDER mode), overwritten.
  * d_hist_vol: optional (NULL ok) double sum of V per bin, overwritten.

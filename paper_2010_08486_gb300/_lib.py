@@ -31,7 +31,7 @@ NOALLOC_MAX_CAND = 65536
 # Every function declared in include/dog.h, in declaration order.
 EXPORTS = (
     "dog_config_default", "dog_create", "dog_destroy", "dog_ladder", "dog_candidates", "dog_prune",
-    "dog_prune_noalloc", "dog_stretch_limits", "dog_stretch", "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_soft_hist",
+    "dog_prune_noalloc", "dog_stretch_limits", "dog_stretch", "dog_render_spheres", "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_soft_hist",
     "dog_backward", "dog_soft_hist_rec", "dog_backward_rec", "dog_debug_dog", "dog_ring_hist_push", "dog_ring_hist_push_batched",
     "dog_profile_enable", "dog_profile_read", "dog_fma_peak",
     "dog_get_status", "dog_test_fail_alloc", "dog_status_string",
@@ -118,6 +118,8 @@ def load(path: str | None = None):
                                           vp, vp]
         lib.dog_stretch_limits.argtypes = [vp, i32, i32, i32, ctypes.c_double, vp, vp, vp]
         lib.dog_stretch.argtypes = [vp, i32, i32, i32, vp, vp, i32, vp]
+        lib.dog_render_spheres.argtypes = [vp, i32, i32, i32, i32, ctypes.c_float, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_uint64, vp, vp, i32, vp]
         lib.dog_volume_hist.argtypes = [vp, vp, vp, i32, vp, vp, vp]
         lib.dog_detect.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp, vp, vp, vp]
         lib.dog_detect_batched.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp]

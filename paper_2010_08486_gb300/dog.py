@@ -145,6 +145,23 @@ def stretch(counts: torch.Tensor, lohi: torch.Tensor | None = None, sat: float =
     return out
 
 
+def render_spheres(spheres: torch.Tensor, h: int, w: int, ss: int = 4, background: float = 0.05,
+                   gain: float = 2000.0, read_noise: float = 4.0, seed: int = 0, with_intensity: bool = False,
+                   stream=None):
+    """Synthetic frame of rendered spheres (dog_render_spheres): 12-bit counts
+    (h, w) as int16 bits (and the noiseless FP32 intensity)."""
+    sp = spheres.contiguous()
+    if sp.dtype != torch.float32 or sp.dim() != 2 or sp.shape[1] != 4 or not sp.is_cuda:
+        raise ValueError("spheres: (n, 4) float32 CUDA tensor (cx, cy, R, A)")
+    counts = torch.empty((h, w), dtype=torch.int16, device=sp.device)
+    inten = torch.empty((h, w), dtype=torch.float32, device=sp.device) if with_intensity else None
+    check(_lib.load().dog_render_spheres(sp.data_ptr() if sp.shape[0] else None, sp.shape[0], h, w, ss,
+                                         float(background), float(gain), float(read_noise), int(seed),
+                                         _ptr(inten), counts.data_ptr(), w, _stream(stream)),
+          "dog_render_spheres")
+    return (counts, inten) if with_intensity else counts
+
+
 class Detector:
     """One handle of the C library on the current CUDA device."""
 
