@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune-cache", default=None, help="JSON file of autotuned tilings (read, then written)")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the 8-stream serving run (0: skip)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched-uneven and differentiable legs")
@@ -192,19 +192,50 @@ def cpu_baseline(frames_u16, budget_s=20.0):
     dt = time.perf_counter() - t0
     line = {"value": n * MP_PER_FRAME / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "%d of the workload's 1024x1024 frames through the whole path (%.1f s)" % (n, dt)}
-    # the same oracle on one core (one frame, in a child process with one OpenMP thread)
-    code = ("import sys, time, numpy as np; sys.path.insert(0, %r); import oracle; "
+    # the same oracle on one core: median over 10 frames, in a child process
+    # with one OpenMP thread
+    code = ("import sys, time, statistics, numpy as np; sys.path.insert(0, %r); import oracle; "
             "from paper_2010_08486_gb300 import synth; "
             "p = oracle.OracleParams(min_sigma=0.8, ratio=1.1, n_levels=25, threshold=0.05); "
-            "img = synth.u16_to_f32(synth.plif_frame_u16(synth.PLIF_SEED_BASE)).astype(np.float64); "
-            "t = time.perf_counter(); oracle.detect(img, p); print(time.perf_counter() - t)") % ROOT
+            "ts = []\n"
+            "for f in range(10):\n"
+            "    img = synth.u16_to_f32(synth.plif_frame_u16(synth.PLIF_SEED_BASE + f)).astype(np.float64)\n"
+            "    t = time.perf_counter(); oracle.detect(img, p); ts.append(time.perf_counter() - t)\n"
+            "print(statistics.median(ts))") % ROOT
     try:
-        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600,
                              env={**os.environ, "OMP_NUM_THREADS": "1"})
         line["value_1core"] = MP_PER_FRAME / float(out.stdout.strip().splitlines()[-1])
+        line["sample_1core"] = "median of 10 frames, one OpenMP thread"
     except (subprocess.SubprocessError, ValueError, IndexError):
         line["value_1core"] = None
+    line["scipy_1core"] = scipy_baseline(frames_u16[:2])
     return line
+
+
+def scipy_baseline(frames_u16):
+    """The composition of library filters that stands in for the paper's
+    scikit-image comparison (Sec. 5): per level scipy.ndimage.gaussian_filter
+    (reflect boundary, truncate 4, FP64), the scaled adjacent differences, a
+    3x3x3 scipy.ndimage.maximum_filter and the threshold; one core (scipy's
+    filters are single-threaded).  Candidates only (no pruning), like the
+    paper's timing."""
+    from scipy import ndimage
+    from paper_2010_08486_gb300 import synth
+    sig = [0.8 * 1.1 ** i for i in range(25)]
+    c = [sig[i] / (sig[i + 1] - sig[i]) for i in range(24)]
+    ts = []
+    n_cand = 0
+    for u in frames_u16:
+        img = synth.u16_to_f32(u).astype(np.float64)
+        t = time.perf_counter()
+        L = np.stack([ndimage.gaussian_filter(img, s, mode="reflect", truncate=4.0) for s in sig])
+        D = np.stack([c[i] * (L[i] - L[i + 1]) for i in range(24)])
+        m = ndimage.maximum_filter(D, size=3, mode="constant", cval=-np.inf)
+        n_cand += int(np.count_nonzero((D == m) & (D > 0.05)))
+        ts.append(time.perf_counter() - t)
+    return {"value": MP_PER_FRAME / statistics.median(ts), "unit": UNIT, "cores": 1, "kind": "scipy composition",
+            "frames": len(ts), "candidates_per_frame": n_cand / max(1, len(ts))}
 
 
 def serve_leg(seconds, local):
@@ -419,6 +450,44 @@ def preprocess_leg(local, frames, cap, table_kw, reps=5):
                     "histogram + limits + stretched FP32 frame, two launches per frame"}
 
 
+def fft_sweep_leg(local, frame, reps=5):
+    """Direct (fused separable passes) against FFT convolution (Sec. 4.1's
+    alternative; Sec. 5 found FFT faster on a V100 for max_sigma > 2 and
+    n_bin > 10): single-frame dog_detect of one 1024x1024 12-bit frame per
+    ladder, geometric from sigma 0.8 to sigma_max with K levels."""
+    import torch
+    from paper_2010_08486_gb300 import _lib, dog
+    s = torch.cuda.current_stream()
+    rows = []
+    for K in (6, 12, 25):
+        for smax in (2.0, 4.0, 8.0, 14.0):
+            ratio = (smax / 0.8) ** (1.0 / (K - 1))
+            row = {"levels": K, "sigma_max": smax}
+            for name, backend in (("direct", _lib.BACKEND_DIRECT), ("fft", _lib.BACKEND_FFT)):
+                try:
+                    det = dog.Detector(dog.plif_config(min_sigma=0.8, ratio=ratio, n_levels=K, backend=backend,
+                                                       blob_cap=65536))
+                except _lib.DogError as e:
+                    row[name + "_ms"] = None
+                    row[name + "_note"] = str(e)
+                    continue
+                blobs = dog.empty_blobs(65536, "cuda")
+                hist = torch.zeros(det.nbins_out, dtype=torch.int32, device="cuda")
+
+                def one():
+                    det.detect(frame, out=blobs, hist=hist, stream=s)
+                for _ in range(3):
+                    one()
+                torch.cuda.synchronize()
+                row[name + "_ms"] = _events_ms(one, reps, s)
+                det.close()
+            if row.get("direct_ms") and row.get("fft_ms"):
+                row["fft_over_direct"] = row["fft_ms"] / row["direct_ms"]
+            rows.append(row)
+    return {"frame": "1024x1024 u16", "calls": "single-frame dog_detect (candidates, pruning, histogram)",
+            "rows": rows}
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -617,14 +686,20 @@ def run_ours(a):
             lat.append(e0.elapsed_time(e1))
     det.set_tiling(0)
     lat.sort()
-    line["latency_ms"] = {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
-                          "frames": len(lat),
-                          "mode": "single frame, dog_detect, %d-row bands (autotuned)" % (lat_tune.band or H)}
+    line["device_latency_ms"] = {"p50": lat[len(lat) // 2],
+                                 "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                                 "kind": "device time: CUDA events around one dog_detect call",
+                                 "frames": len(lat),
+                                 "mode": "single frame, dog_detect, %d-row bands (autotuned)" % (lat_tune.band or H)}
 
     if not a.no_forms:
         line["preprocess"] = preprocess_leg(local, flist, cap, {"out": out, "counts": counts, "hists": hists})
+        line["fft_sweep"] = fft_sweep_leg(local, flist[0])
     if a.serve_seconds > 0:
         line["serve"] = serve_leg(a.serve_seconds, local)
+        line["latency_ms"] = {"p50": line["serve"]["p50_ms"], "p99": line["serve"]["p99_ms"],
+                              "kind": "arrival to the results on the host, 8 camera streams at 2000 frames/s "
+                                      "for %.0f s (continuous batching)" % a.serve_seconds}
     if not a.no_forms:
         line["batched_uneven"] = batched_leg(local, a.tune_cache)
         line["differentiable"] = diff_leg(local)

@@ -58,6 +58,7 @@ enum { DOG_NORM_DERIV = 0, DOG_NORM_PAPER = 1 };
 enum { DOG_PRUNE_COALESCE = 0, DOG_PRUNE_SUPPRESS = 1, DOG_PRUNE_OFF = 2 };
 enum { DOG_HIST_LOGV = 0, DOG_HIST_LADDER = 1 };
 enum { DOG_DTYPE_F32 = 0, DOG_DTYPE_U16 = 1 };
+enum { DOG_BACKEND_DIRECT = 0, DOG_BACKEND_FFT = 1 };
 
 /* Largest ladder and radius this build accepts. */
 #define DOG_MAX_LEVELS 32
@@ -94,6 +95,16 @@ enum { DOG_DTYPE_F32 = 0, DOG_DTYPE_U16 = 1 };
  *             [0, 1] with its own limits as in dog_stretch_limits/dog_stretch
  *             (computed on the device before the detection kernel, applied as
  *             the kernel loads the counts); FP32 frames are used as given.
+ *  backend    DIRECT: the fused separable passes (default).  FFT: the scale
+ *             space by FFT convolution (Sec. 4.1's alternative): the frame,
+ *             reflect-padded by the largest radius, is transformed once and
+ *             each level is the inverse transform of its product with the
+ *             level's kernel spectrum (single precision), then the same DoG,
+ *             3x3x3 test and threshold.  Used by dog_candidates, dog_detect
+ *             and dog_debug_dog; dog_detect_batched returns UNSUPPORTED and the
+ *             differentiable form always uses the direct passes.  Its
+ *             workspace (about 10 K max_h max_w bytes) is allocated by the
+ *             first such call.
  */
 typedef struct dog_config {
     int32_t n_levels;
@@ -107,6 +118,7 @@ typedef struct dog_config {
     int32_t max_h, max_w;
     int32_t blob_cap;
     double stretch_sat;
+    int32_t backend;
 } dog_config;
 
 /* One blob: centre (x, y), DoG plane, sigma (the plane's sigma, or the mean

@@ -24,6 +24,7 @@ NORM_DERIV, NORM_PAPER = 0, 1
 PRUNE_COALESCE, PRUNE_SUPPRESS, PRUNE_OFF = 0, 1, 2
 HIST_LOGV, HIST_LADDER = 0, 1
 DTYPE_F32, DTYPE_U16 = 0, 1
+BACKEND_DIRECT, BACKEND_FFT = 0, 1
 MAX_LEVELS = 32
 MAX_RADIUS = 64
 NOALLOC_MAX_CAND = 65536
@@ -58,6 +59,7 @@ class DogConfig(ctypes.Structure):
         ("max_w", ctypes.c_int32),
         ("blob_cap", ctypes.c_int32),
         ("stretch_sat", ctypes.c_double),
+        ("backend", ctypes.c_int32),
     ]
 
 

@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if (force or not os.path.exists(LIB)
             or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs)):
         tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [_nvcc(), "-shared", ARCH, "-o", tmp] + objs + ["-lcudart"]
+        cmd = [_nvcc(), "-shared", ARCH, "-o", tmp] + objs + ["-lcudart", "-lcufft"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -93,6 +93,8 @@ struct dog_handle {
     int* d_slohi = nullptr;
     int* d_bshist = nullptr;
     int* d_bslohi = nullptr;
+    // FFT backend (created by its first call)
+    FftWS* fft = nullptr;
     // differentiable form
     void* soft_ws = nullptr;
     cudaStream_t last = nullptr;
@@ -258,6 +260,7 @@ int dog_config_default(dog_config* c) {
     c->max_w = 1024;
     c->blob_cap = 65536;
     c->stretch_sat = 0.0;
+    c->backend = DOG_BACKEND_DIRECT;
     return DOG_OK;
 }
 
@@ -272,6 +275,7 @@ int dog_create(const dog_config* cfg, dog_t** out) {
     if (c.norm != DOG_NORM_DERIV && c.norm != DOG_NORM_PAPER) return DOG_ERR_INVALID;
     if (c.prune < DOG_PRUNE_COALESCE || c.prune > DOG_PRUNE_OFF) return DOG_ERR_INVALID;
     if (c.hist_mode != DOG_HIST_LOGV && c.hist_mode != DOG_HIST_LADDER) return DOG_ERR_INVALID;
+    if (c.backend != DOG_BACKEND_DIRECT && c.backend != DOG_BACKEND_FFT) return DOG_ERR_INVALID;
 
     dog_handle* h = new (std::nothrow) dog_handle();
     if (!h) return DOG_ERR_NOMEM;
@@ -483,6 +487,7 @@ void dog_destroy(dog_t* h) {
     cudaDeviceSynchronize();
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     dogk::soft_free(h);
+    dogk::fft_free(h->fft);
     free_all(h);
     delete h;
 }
@@ -580,6 +585,19 @@ static ResolveParams resolve_params(const dog_handle* h, const FusedParams& f) {
     return r;
 }
 
+// The FFT backend's workspace, built on first use from the handle's kernels.
+static int fft_ws(dog_handle* h) {
+    if (h->fft) return DOG_OK;
+    std::vector<std::vector<double>> w(h->K);
+    for (int i = 0; i < h->K; ++i) {
+        const int r = h->rad[i];
+        double z = 0.0;
+        for (int j = -r; j <= r; ++j) z += std::exp(-(double)j * j / (2.0 * h->sig[i] * h->sig[i]));
+        for (int j = -r; j <= r; ++j) w[i].push_back(std::exp(-(double)j * j / (2.0 * h->sig[i] * h->sig[i])) / z);
+    }
+    return fft_create(&h->fft, h->cfg.max_h, h->cfg.max_w, h->K, h->R, w);
+}
+
 int dog_candidates(dog_t* h, const void* d_img, int32_t dtype, int32_t H, int32_t W, int32_t pitch,
                    dog_blob* d_blobs, int32_t cap, int32_t* d_count, void* stream) {
     if (!h || !d_blobs || !d_count || cap < 0) return DOG_ERR_INVALID;
@@ -588,6 +606,14 @@ int dog_candidates(dog_t* h, const void* d_img, int32_t dtype, int32_t H, int32_
     cudaStream_t s = (cudaStream_t)stream;
     h->last = s;
     FusedParams p = frame_params(h, d_img, dtype, H, W, pitch);
+    if (h->cfg.backend == DOG_BACKEND_FFT) {
+        if (H > h->cfg.max_h || W > h->cfg.max_w) return DOG_ERR_INVALID;
+        st = fft_ws(h);
+        if (st != DOG_OK) return st;
+        if (p.dtype == DTYPE_U16_STRETCH) DOG_CUDA(single_limits(h, d_img, H, W, pitch, s));
+        return fft_run(h->fft, d_img, p.dtype, H, W, pitch, h->d_slohi, h->P, h->d_c, (float)h->cfg.threshold,
+                       MODE_CANDIDATES, d_blobs, cap, d_count, nullptr, h->d_status, s);
+    }
     p.mode = MODE_CANDIDATES;
     p.blobs = d_blobs;
     p.cap = cap;
@@ -612,6 +638,14 @@ int dog_debug_dog(dog_t* h, const void* d_img, int32_t dtype, int32_t H, int32_t
     cudaStream_t s = (cudaStream_t)stream;
     h->last = s;
     FusedParams p = frame_params(h, d_img, dtype, H, W, pitch);
+    if (h->cfg.backend == DOG_BACKEND_FFT) {
+        if (H > h->cfg.max_h || W > h->cfg.max_w) return DOG_ERR_INVALID;
+        st = fft_ws(h);
+        if (st != DOG_OK) return st;
+        if (p.dtype == DTYPE_U16_STRETCH) DOG_CUDA(single_limits(h, d_img, H, W, pitch, s));
+        return fft_run(h->fft, d_img, p.dtype, H, W, pitch, h->d_slohi, h->P, h->d_c, (float)h->cfg.threshold,
+                       MODE_DUMP, nullptr, 0, nullptr, d_dog, h->d_status, s);
+    }
     p.mode = MODE_DUMP;
     p.dump = d_dog;
     if (p.dtype == DTYPE_U16_STRETCH) DOG_CUDA(single_limits(h, d_img, H, W, pitch, s));
@@ -759,6 +793,7 @@ static int grow_batch(dog_handle* h, int n) {
 int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t max_h, int32_t max_w,
                        dog_blob* d_blobs, int32_t* d_counts, uint32_t* d_hists, void* stream) {
     if (!h || !d_frames || n < 1 || !d_blobs || !d_counts || max_h < 1 || max_w < 1) return DOG_ERR_INVALID;
+    if (h->cfg.backend != DOG_BACKEND_DIRECT) return DOG_ERR_UNSUPPORTED;
     const bool stretch = h->cfg.stretch_sat > 0.0;
     if (stretch && (long long)max_h * max_w >= (1LL << 31)) return DOG_ERR_UNSUPPORTED;
     int st = grow_batch(h, n);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "dog.h"
 
 namespace dogk {
@@ -162,6 +164,13 @@ cudaError_t launch_batch_prep(const dog_frame* frames, int n, int band, int tail
 // frame (frames == nullptr) or of the U16 frames of a device frame table
 cudaError_t launch_stretch_limits(const dog_frame* frames, int n, const uint16_t* img, int H, int W, int pitch,
                                   double sat, int num_sms, int* hist, int* lohi, cudaStream_t s);
+// FFT-convolution backend (dog_fft.cu)
+struct FftWS;
+int fft_create(FftWS** out, int max_h, int max_w, int K, int R, const std::vector<std::vector<double>>& w);
+void fft_free(FftWS* f);
+int fft_run(FftWS* f, const void* img, int dtype, int H, int W, int pitch, const int* lohi, int P,
+            const float* c, float thr, int mode, dog_blob* blobs, int cap, int* count, float* dump, int* status,
+            cudaStream_t s);
 cudaError_t launch_stretch_apply(const uint16_t* img, int H, int W, int pitch, const int* lohi, float* out,
                                  int out_pitch, int num_sms, cudaStream_t s);
 

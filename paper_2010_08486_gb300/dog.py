@@ -37,6 +37,7 @@ class DetectorConfig:
     max_w: int = 1024
     blob_cap: int = 65536
     stretch_sat: float = 0.0
+    backend: int = _lib.BACKEND_DIRECT
 
     def to_c(self):
         c = _lib.DogConfig()
