@@ -456,7 +456,7 @@ def fft_sweep_leg(local, frame, reps=5):
     n_bin > 10): single-frame dog_detect of one 1024x1024 12-bit frame per
     ladder, geometric from sigma 0.8 to sigma_max with K levels."""
     import torch
-    from paper_2010_08486_gb300 import _lib, dog
+    from paper_2010_08486_gb300 import _lib, autotune, dog
     s = torch.cuda.current_stream()
     rows = []
     for K in (6, 12, 25):
@@ -471,6 +471,8 @@ def fft_sweep_leg(local, frame, reps=5):
                     row[name + "_ms"] = None
                     row[name + "_note"] = str(e)
                     continue
+                if backend == _lib.BACKEND_DIRECT:   # row bands for a single frame, as the latency path
+                    row["direct_band_rows"] = autotune.tune_detector_frame(det, frame).band
                 blobs = dog.empty_blobs(65536, "cuda")
                 hist = torch.zeros(det.nbins_out, dtype=torch.int32, device="cuda")
 
@@ -484,8 +486,8 @@ def fft_sweep_leg(local, frame, reps=5):
             if row.get("direct_ms") and row.get("fft_ms"):
                 row["fft_over_direct"] = row["fft_ms"] / row["direct_ms"]
             rows.append(row)
-    return {"frame": "1024x1024 u16", "calls": "single-frame dog_detect (candidates, pruning, histogram)",
-            "rows": rows}
+    return {"frame": "1024x1024 u16", "calls": "single-frame dog_detect (candidates, pruning, histogram); "
+            "direct: autotuned row bands", "rows": rows}
 
 
 def run_reference(a):

@@ -104,7 +104,9 @@ enum { DOG_BACKEND_DIRECT = 0, DOG_BACKEND_FFT = 1 };
  *             and dog_debug_dog; dog_detect_batched returns UNSUPPORTED and the
  *             differentiable form always uses the direct passes.  Its
  *             workspace (about 10 K max_h max_w bytes) is allocated by the
- *             first such call.
+ *             first such call.  An FFT handle may hold a ladder whose direct
+ *             passes would not fit in shared memory; its differentiable calls
+ *             then return UNSUPPORTED.
  */
 typedef struct dog_config {
     int32_t n_levels;

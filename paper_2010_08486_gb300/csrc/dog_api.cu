@@ -95,6 +95,7 @@ struct dog_handle {
     int* d_bslohi = nullptr;
     // FFT backend (created by its first call)
     FftWS* fft = nullptr;
+    bool direct_ok = true;   // the fused kernel's shared memory fits this device
     // differentiable form
     void* soft_ws = nullptr;
     cudaStream_t last = nullptr;
@@ -404,7 +405,10 @@ int dog_create(const dog_config* cfg, dog_t** out) {
         delete h;
         return DOG_ERR_CUDA;
     }
-    if (b.smem_bytes + 4096 > optin) { delete h; return DOG_ERR_UNSUPPORTED; }
+    // the fused kernel's shared memory must fit; an FFT-backend handle can do
+    // without it (its differentiable and batched calls then report UNSUPPORTED)
+    h->direct_ok = b.smem_bytes + 4096 <= optin;
+    if (!h->direct_ok && c.backend == DOG_BACKEND_DIRECT) { delete h; return DOG_ERR_UNSUPPORTED; }
 
     // ---- pruning conflict table and histogram tables
     std::vector<int> d2(h->P * h->P);
@@ -478,6 +482,7 @@ int dog_create(const dog_config* cfg, dog_t** out) {
     b.w = h->d_w;
     b.c = h->d_c;
     b.status = h->d_status;
+
     *out = h;
     return DOG_OK;
 }
@@ -793,7 +798,7 @@ static int grow_batch(dog_handle* h, int n) {
 int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t max_h, int32_t max_w,
                        dog_blob* d_blobs, int32_t* d_counts, uint32_t* d_hists, void* stream) {
     if (!h || !d_frames || n < 1 || !d_blobs || !d_counts || max_h < 1 || max_w < 1) return DOG_ERR_INVALID;
-    if (h->cfg.backend != DOG_BACKEND_DIRECT) return DOG_ERR_UNSUPPORTED;
+    if (h->cfg.backend != DOG_BACKEND_DIRECT || !h->direct_ok) return DOG_ERR_UNSUPPORTED;
     const bool stretch = h->cfg.stretch_sat > 0.0;
     if (stretch && (long long)max_h * max_w >= (1LL << 31)) return DOG_ERR_UNSUPPORTED;
     int st = grow_batch(h, n);
@@ -867,6 +872,7 @@ int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t m
 int dog_soft_hist(dog_t* h, const float* d_img, int32_t H, int32_t W, int32_t pitch, const float* d_sigmas,
                   float* d_soft_hist, void* stream) {
     if (!h || !d_sigmas || !d_soft_hist) return DOG_ERR_INVALID;
+    if (!h->direct_ok) return DOG_ERR_UNSUPPORTED;
     int st = check_frame(h, d_img, DOG_DTYPE_F32, H, W, pitch);
     if (st != DOG_OK) return st;
     h->last = (cudaStream_t)stream;
@@ -876,6 +882,7 @@ int dog_soft_hist(dog_t* h, const float* d_img, int32_t H, int32_t W, int32_t pi
 int dog_soft_hist_rec(dog_t* h, const float* d_img, int32_t H, int32_t W, int32_t pitch, const float* d_sigmas,
                       float* d_soft_hist, dog_soft_max* d_max, int32_t cap, int32_t* d_count, void* stream) {
     if (!h || !d_sigmas || !d_soft_hist || !d_max || !d_count || cap < 1) return DOG_ERR_INVALID;
+    if (!h->direct_ok) return DOG_ERR_UNSUPPORTED;
     int st = check_frame(h, d_img, DOG_DTYPE_F32, H, W, pitch);
     if (st != DOG_OK) return st;
     h->last = (cudaStream_t)stream;
@@ -887,6 +894,7 @@ int dog_backward_rec(dog_t* h, const float* d_img, int32_t H, int32_t W, int32_t
                      float* d_grad_img, float* d_grad_sigmas, void* stream) {
     if (!h || !d_sigmas || !d_max || !d_count || cap < 1 || !d_grad_hist || !d_grad_img || !d_grad_sigmas)
         return DOG_ERR_INVALID;
+    if (!h->direct_ok) return DOG_ERR_UNSUPPORTED;
     int st = check_frame(h, d_img, DOG_DTYPE_F32, H, W, pitch);
     if (st != DOG_OK) return st;
     h->last = (cudaStream_t)stream;
@@ -897,6 +905,7 @@ int dog_backward_rec(dog_t* h, const float* d_img, int32_t H, int32_t W, int32_t
 int dog_backward(dog_t* h, const float* d_img, int32_t H, int32_t W, int32_t pitch, const float* d_sigmas,
                  const float* d_grad_hist, float* d_grad_img, float* d_grad_sigmas, void* stream) {
     if (!h || !d_sigmas || !d_grad_hist || !d_grad_img || !d_grad_sigmas) return DOG_ERR_INVALID;
+    if (!h->direct_ok) return DOG_ERR_UNSUPPORTED;
     int st = check_frame(h, d_img, DOG_DTYPE_F32, H, W, pitch);
     if (st != DOG_OK) return st;
     h->last = (cudaStream_t)stream;

@@ -100,3 +100,20 @@ def test_fft_batched_is_unsupported():
     with pytest.raises(_lib.DogError) as e:
         det.detect_batched([img])
     assert e.value.code == _lib.DOG_ERR_UNSUPPORTED
+
+
+def test_fft_ladder_beyond_direct_shared_memory():
+    """25 levels up to sigma 14 (radii to 56) do not fit the fused kernel's
+    shared memory; the FFT backend still builds and matches the oracle, while
+    the direct backend reports UNSUPPORTED."""
+    ratio = (14.0 / 0.8) ** (1.0 / 24)
+    with pytest.raises(_lib.DogError) as e:
+        dog.Detector(dog.plif_config(ratio=ratio, max_h=384, max_w=384))
+    assert e.value.code == _lib.DOG_ERR_UNSUPPORTED
+    cfg = dog.plif_config(ratio=ratio, backend=_lib.BACKEND_FFT, max_h=384, max_w=384)
+    u16 = synth.plif_frame_u16(synth.PLIF_SEED_BASE + 10, 384, 384)
+    det = _check(cfg, synth.u16_to_f32(u16), u16, "plif_384_sigma14")
+    sig = torch.ones(det.K, dtype=torch.float32, device="cuda")
+    with pytest.raises(_lib.DogError) as e2:
+        det.soft_hist(torch.zeros((384, 384), dtype=torch.float32, device="cuda"), sig)
+    assert e2.value.code == _lib.DOG_ERR_UNSUPPORTED
