@@ -54,7 +54,7 @@ def parse():
                     help="length of the 8-stream serving run (0: skip)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched-uneven and differentiable legs")
-    ap.add_argument("--leg", choices=["batched", "differentiable"], default=None,
+    ap.add_argument("--leg", choices=["batched", "differentiable", "preprocess", "fft", "spheres"], default=None,
                     help="run only this form and print its JSON object (a profiling entry point)")
     return ap.parse_args()
 
@@ -490,6 +490,56 @@ def fft_sweep_leg(local, frame, reps=5):
             "direct: autotuned row bands", "rows": rows}
 
 
+def spheres_leg(local, n_frames=8, reps=3):
+    """The paper's evaluation data (Sec. 5): 1000x1000 frames of 100 rendered
+    spheres with shot and read noise (dog_render_spheres), rendered on the GPU,
+    then contrast stretched (0.35%) and detected; throughput of the renderer
+    and of the detection, and PASCAL-VOC precision/recall (disc IoU >= 0.5)
+    against the spheres (Sec. 5 reports precision and recall)."""
+    import torch
+    from paper_2010_08486_gb300 import dog, quality, synth
+    s = torch.cuda.current_stream()
+    tables = [synth.sphere_table(synth.SPHERE_SEED_BASE + 300 + f, n=100, h=1000, w=1000, r_range=(4.0, 16.0))
+              for f in range(n_frames)]
+    dev_tables = [torch.from_numpy(t).cuda() for t in tables]
+    frames = [torch.empty((1000, 1000), dtype=torch.int16, device="cuda") for _ in range(n_frames)]
+    lib = dog._lib.load()
+
+    def render():
+        for f in range(n_frames):
+            lib.dog_render_spheres(dev_tables[f].data_ptr(), 100, 1000, 1000, 4, 0.05, 2000.0, 4.0,
+                                   synth.SPHERE_SEED_BASE + 300 + f, None, frames[f].data_ptr(), 1000, s.cuda_stream)
+    render()
+    torch.cuda.synchronize()
+    ms_r = _events_ms(render, reps, s)
+    det = dog.Detector(dog.DetectorConfig(min_sigma=2.0, ratio=1.15, n_levels=14, threshold=0.05, max_h=1000,
+                                          max_w=1000, blob_cap=16384, stretch_sat=0.0035))
+    cap = 16384
+    table = det.frame_table(frames, cap)
+    out = torch.empty((n_frames * cap, 5), dtype=torch.int32, device="cuda")
+    counts = torch.zeros(n_frames, dtype=torch.int32, device="cuda")
+    hists = torch.zeros((n_frames, det.nbins_out), dtype=torch.int32, device="cuda")
+
+    def detect():
+        det.detect_batched(None, table=table, out=out, counts=counts, hists=hists, stream=s)
+    detect()
+    torch.cuda.synchronize()
+    ms_d = _events_ms(detect, reps, s)
+    c = counts.cpu().numpy()
+    P, R = [], []
+    for f in range(n_frames):
+        x, y, l, sg, r = dog.blobs_from_raw(out[f * cap:(f + 1) * cap], int(c[f]))
+        m = quality.match(quality.blob_circles(x, y, sg), r, tables[f][:, :3])
+        P.append(m.precision)
+        R.append(m.recall)
+    mp = n_frames * 1.0
+    return {"frames": n_frames, "spheres_per_frame": 100, "frame": "1000x1000", "render_ms": ms_r,
+            "render_mp_per_s": mp / (ms_r / 1e3), "detect_ms": ms_d, "detect_mp_per_s": mp / (ms_d / 1e3),
+            "ladder": "sigma 2 * 1.15^i, 14 levels, threshold 0.05, stretch 0.35%",
+            "precision": float(np.mean(P)), "recall": float(np.mean(R)),
+            "matching": "PASCAL VOC, disc IoU >= 0.5, detections by decreasing response"}
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -697,6 +747,7 @@ def run_ours(a):
     if not a.no_forms:
         line["preprocess"] = preprocess_leg(local, flist, cap, {"out": out, "counts": counts, "hists": hists})
         line["fft_sweep"] = fft_sweep_leg(local, flist[0])
+        line["spheres"] = spheres_leg(local)
     if a.serve_seconds > 0:
         line["serve"] = serve_leg(a.serve_seconds, local)
         line["latency_ms"] = {"p50": line["serve"]["p50_ms"], "p99": line["serve"]["p99_ms"],
@@ -720,7 +771,27 @@ def run_leg(a):
     libbuild.build()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    res = batched_leg(local, a.tune_cache) if a.leg == "batched" else diff_leg(local)
+    if a.leg == "batched":
+        res = batched_leg(local, a.tune_cache)
+    elif a.leg == "differentiable":
+        res = diff_leg(local)
+    elif a.leg == "spheres":
+        res = spheres_leg(local)
+    else:
+        import torch
+        from paper_2010_08486_gb300 import synth
+        B = 16
+        counts_u16 = make_frames(B, synth.PLIF_SEED_BASE)
+        frames = torch.from_numpy(np.stack([c.view(np.int16) for c in counts_u16])).cuda()
+        flist = [frames[i] for i in range(B)]
+        if a.leg == "preprocess":
+            cap = 16384
+            kw = {"out": torch.empty((B * cap, 5), dtype=torch.int32, device="cuda"),
+                  "counts": torch.zeros(B, dtype=torch.int32, device="cuda"),
+                  "hists": torch.zeros((B, 32), dtype=torch.int32, device="cuda")}
+            res = preprocess_leg(local, flist, cap, kw)
+        else:
+            res = fft_sweep_leg(local, flist[0])
     print(json.dumps({"leg": a.leg, **res}))
 
 
