@@ -7,7 +7,7 @@
 // Design.  A CTA owns a strip of TX = 32 output columns and walks down a
 // band of rows in blocks of MB = 8 rows, so every input pixel of the strip
 // is read once from global memory for all K scales and no vertical halo is
-// recomputed.  Each of the eight warps owns a fixed set of levels, chosen on
+// recomputed.  Each of the twelve producer warps owns a fixed set of levels, chosen on
 // the host to balance taps.  For each block and owned level a warp
 //   1. runs the horizontal pass of the next 8 input rows into the level's
 //      circular shared-memory ring (which runs Tpad/8 blocks ahead),
@@ -182,9 +182,9 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
     const int yorg = yb0 - MB * emax;   // input-ring slot origin
     float* in = sm + p.in_off;
     float* dbuf = sm + p.d_off;
-    // each producer warp fetches one of the MB rows a block adds (NWARPS == MB),
+    // producer warps 0 .. MB-1 each fetch one of the MB rows a block adds,
     // lane x columns x, x + 32, ... of the TX + 2R loaded ones
-    static_assert(NWARPS == MB, "one prefetched row per producer warp");
+    static_assert(NWARPS >= MB, "one prefetched row per producer warp");
     constexpr int NPF = (TX + 2 * DOG_MAX_RADIUS + 31) / 32;
 
     for (int b = -emax; b < nblk; ++b) {
@@ -192,7 +192,7 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
         // prefetch the 8 rows block b+1 adds (latency hidden behind the passes)
         unsigned pf[NPF];   // raw pixel bits; converted when stored, after the passes
         const int ynew = yorg + MB * (b + emax + 1) + p.dmax;
-        const bool do_pf = b + 1 < nblk;
+        const bool do_pf = b + 1 < nblk && warp < MB;
         const int yrow = refl(ynew + warp, tc.H);
 #pragma unroll
         for (int k = 0; k < NPF; ++k) {
