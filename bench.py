@@ -333,28 +333,36 @@ def batched_leg(local, cache_path, reps=5):
         shp = tuple(frames[f].shape)
         if shp not in bands:
             det.set_tiling(0)
-            bands[shp] = autotune.tune_detector_frame(det, frames[f], cache_path=cache_path).band
+            r = autotune.tune_detector_frame(det, frames[f], cache_path=cache_path)
+            bands[shp] = (r.band, r.producer_warps)
+
+    def use_tiling(f):
+        band, nw = bands[tuple(frames[f].shape)]
+        det.set_producer_warps(nw)
+        det.set_tiling(band)
     blobs = dog.empty_blobs(cap, "cuda")
     hist1 = torch.zeros(det.nbins_out, dtype=torch.int32, device="cuda")
     c_single = torch.zeros(n, dtype=torch.int32)
 
     def per_frame():
         for f in range(n):
-            det.set_tiling(bands[tuple(frames[f].shape)])
+            use_tiling(f)
             det.detect(frames[f], out=blobs, hist=hist1, stream=s)
     with torch.cuda.stream(s):
         per_frame()
         torch.cuda.synchronize()
         ms_p = _events_ms(per_frame, 2, s)
         for f in range(n):   # counts of the plain path (same frames)
-            det.set_tiling(bands[tuple(frames[f].shape)])
+            use_tiling(f)
             det.detect(frames[f], out=blobs, hist=hist1, stream=s)
             c_single[f] = int(blobs.count.item())
     assert det.status() == 0
     return {"frames": n, "megapixels": round(mp_total, 3), "band_rows": tuned.band,
+            "producer_warps": tuned.producer_warps,
             "graph_replay_ms": ms_b, "mp_per_s": mp_total / (ms_b / 1e3),
             "per_frame_ms": ms_p, "per_frame_mp_per_s": mp_total / (ms_p / 1e3),
-            "per_frame_band_rows": {"%dx%d" % k: v for k, v in sorted(bands.items())},
+            "per_frame_band_rows": {"%dx%d" % k: v[0] for k, v in sorted(bands.items())},
+            "per_frame_producer_warps": {"%dx%d" % k: v[1] for k, v in sorted(bands.items())},
             "speedup_vs_per_frame": ms_p / ms_b,
             "same_blob_counts_as_per_frame": bool(torch.equal(c_batched, c_single)),
             "dtype": "f32"}
@@ -399,7 +407,8 @@ def diff_leg(local, reps=3):
     fwd()
     ms_f = _events_ms(fwd, reps, s)
     mp = B * 1024 * 1024 / 1e6
-    return {"frames": B, "sigmas": 12, "band_rows": tuned.band, "fwd_bwd_ms": ms, "mp_per_s": mp / (ms / 1e3),
+    return {"frames": B, "sigmas": 12, "band_rows": tuned.band, "producer_warps": tuned.producer_warps,
+            "fwd_bwd_ms": ms, "mp_per_s": mp / (ms / 1e3),
             "plain_detect_ms": ms_f, "plain_mp_per_s": mp / (ms_f / 1e3), "ratio_to_plain": ms / ms_f,
             "dtype": "f32 (f64 sigma-gradient sums)"}
 
@@ -655,7 +664,7 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {**workload_config(B), "band_rows": tuned.band or H,
+            "config": {**workload_config(B), "band_rows": tuned.band or H, "producer_warps": tuned.producer_warps,
                        "tiling": "32-column strips x autotuned row bands, 1 CTA per SM, persistent"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": traffic,

@@ -287,6 +287,19 @@ int dog_detect_batched(dog_t* h, const dog_frame* d_frames, int32_t n, int32_t h
  * frames) and the persistent grid multiplier; set by the autotuner. */
 int dog_set_tiling(dog_t* h, int32_t band_rows, int32_t ctas_per_sm);
 
+/* Producer warps of the detection kernel form: 8 (168 registers each) or 12
+ * (128 each), or 0 for the handle's default choice (12 for ladders of 20 or
+ * more levels whose largest level fits an even share of 12 warps, else 8).
+ * Results do not depend on it: every level is computed by the same
+ * operations in either form.  Set by the autotuner; the scale levels are
+ * re-balanced over the chosen warps on the host.  Not safe to call while a
+ * launch on this handle is being issued from another thread.
+ * Errors: INVALID (n not 0, 8 or 12). */
+int dog_set_producer_warps(dog_t* h, int32_t n);
+
+/* The handle's current producer-warp count (8 or 12), or INVALID for NULL. */
+int dog_get_producer_warps(const dog_t* h);
+
 /* Differentiable form (not in the paper; used to tune the ladder).  Soft
  * histogram over the hard 3x3x3 local maxima of D (no threshold):
  *   H_b += sum_v sigmoid((D_v - threshold) / soft_T) kappa_b(t(sigma_l(v)))

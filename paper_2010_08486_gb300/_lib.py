@@ -32,7 +32,7 @@ NOALLOC_MAX_CAND = 65536
 # Every function declared in include/dog.h, in declaration order.
 EXPORTS = (
     "dog_config_default", "dog_create", "dog_destroy", "dog_ladder", "dog_candidates", "dog_prune",
-    "dog_prune_noalloc", "dog_stretch_limits", "dog_stretch", "dog_render_spheres", "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_soft_hist",
+    "dog_prune_noalloc", "dog_stretch_limits", "dog_stretch", "dog_render_spheres", "dog_volume_hist", "dog_detect", "dog_detect_batched", "dog_set_tiling", "dog_set_producer_warps", "dog_get_producer_warps", "dog_soft_hist",
     "dog_backward", "dog_soft_hist_rec", "dog_backward_rec", "dog_debug_dog", "dog_ring_hist_push", "dog_ring_hist_push_batched",
     "dog_profile_enable", "dog_profile_read", "dog_fma_peak",
     "dog_get_status", "dog_test_fail_alloc", "dog_status_string",
@@ -126,6 +126,8 @@ def load(path: str | None = None):
         lib.dog_detect.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp, vp, vp, vp]
         lib.dog_detect_batched.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp]
         lib.dog_set_tiling.argtypes = [vp, i32, i32]
+        lib.dog_set_producer_warps.argtypes = [vp, i32]
+        lib.dog_get_producer_warps.argtypes = [vp]
         lib.dog_soft_hist.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp]
         lib.dog_backward.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
         lib.dog_soft_hist_rec.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, i32, vp, vp]

@@ -10,8 +10,9 @@ the frame shapes, the ladder and the number of SMs, so it is measured.
 The tuner ranks candidate band heights with a cost model (waves x rows walked,
 the halo counted as half a row because only its horizontal pass runs), times
 the best few on the device through the detector's own entry points, and keeps
-the winner per (shapes, ladder) key.  The timing function is injectable, so
-the selection logic runs on the CPU in tests.
+the winner per (shapes, ladder) key.  It also times both kernel forms (8 or 12
+producer warps; which is faster depends on the ladder).  The timing function
+is injectable, so the selection logic runs on the CPU in tests.
 """
 from __future__ import annotations
 
@@ -85,12 +86,16 @@ def candidate_bands(shapes: Sequence[Tuple[int, int]], radii: Sequence[int], n_s
     return out
 
 
+PRODUCER_WARPS = (12, 8)   # kernel forms (0: the handle's default)
+
+
 @dataclass
 class TuneResult:
     band: int
     ctas_per_sm: int
     ms: float
     timings: Dict[str, float] = field(default_factory=dict)
+    producer_warps: int = 0
 
 
 def shapes_key(shapes: Iterable[Tuple[int, int]], radii: Sequence[int], n_sm: int, mode: str) -> str:
@@ -104,9 +109,9 @@ def shapes_key(shapes: Iterable[Tuple[int, int]], radii: Sequence[int], n_sm: in
 class Autotuner:
     """Chooses band heights (and CTAs per SM) for a Detector by timing.
 
-    measure(band, ctas_per_sm) -> milliseconds is supplied by the caller or
-    built by `frame_measure` / `batch_measure`; results are cached per key and
-    can be saved to / loaded from a JSON file."""
+    measure(band, ctas_per_sm, producer_warps) -> milliseconds is supplied by
+    the caller or built by `frame_measure` / `batch_measure`; results are
+    cached per key and can be saved to / loaded from a JSON file."""
 
     def __init__(self, n_sm: int, radii: Sequence[int], cache_path: Optional[str] = None):
         self.n_sm = n_sm
@@ -116,21 +121,23 @@ class Autotuner:
         if cache_path and os.path.exists(cache_path):
             self.load(cache_path)
 
-    def tune(self, shapes: Sequence[Tuple[int, int]], measure: Callable[[int, int], float], mode: str = "frame",
-             ctas_options: Sequence[int] = (1,), limit: int = 4) -> TuneResult:
+    def tune(self, shapes: Sequence[Tuple[int, int]], measure: Callable[[int, int, int], float],
+             mode: str = "frame", ctas_options: Sequence[int] = (1,), limit: int = 4,
+             nw_options: Sequence[int] = PRODUCER_WARPS) -> TuneResult:
         key = shapes_key(shapes, self.radii, self.n_sm, mode)
         if key in self.cache:
             return self.cache[key]
         best: Optional[TuneResult] = None
         timings: Dict[str, float] = {}
-        for cps in ctas_options:
-            for band in candidate_bands(shapes, self.radii, self.n_sm, cps, limit):
-                ms = float(measure(band, cps))
-                timings["%d/%d" % (band, cps)] = ms
-                if not math.isfinite(ms):
-                    continue
-                if best is None or ms < best.ms:
-                    best = TuneResult(band, cps, ms)
+        for nw in nw_options:
+            for cps in ctas_options:
+                for band in candidate_bands(shapes, self.radii, self.n_sm, cps, limit):
+                    ms = float(measure(band, cps, nw))
+                    timings["%d/%d/%d" % (band, cps, nw)] = ms
+                    if not math.isfinite(ms):
+                        continue
+                    if best is None or ms < best.ms:
+                        best = TuneResult(band, cps, ms, producer_warps=nw)
         if best is None:
             raise RuntimeError("autotune: no candidate tiling could be timed")
         best.timings = timings
@@ -148,7 +155,8 @@ class Autotuner:
             raw = json.load(f)
         for k, v in raw.items():
             self.cache[k] = TuneResult(int(v["band"]), int(v["ctas_per_sm"]), float(v["ms"]),
-                                       {str(a): float(b) for a, b in v.get("timings", {}).items()})
+                                       {str(a): float(b) for a, b in v.get("timings", {}).items()},
+                                       int(v.get("producer_warps", 0)))
 
 
 def _time_ms(fn, reps: int, warm: int = 2) -> float:
@@ -165,32 +173,31 @@ def _time_ms(fn, reps: int, warm: int = 2) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def frame_measure(det, frame, reps: int = 5) -> Callable[[int, int], float]:
+def _measure_with(det, fn, reps: int) -> Callable[[int, int, int], float]:
+    def measure(band: int, cps: int, nw: int = 0) -> float:
+        nw0 = det.producer_warps
+        det.set_producer_warps(nw)
+        det.set_tiling(band, cps)
+        try:
+            return _time_ms(fn, reps)
+        finally:
+            det.set_tiling(0, 1)
+            det.set_producer_warps(nw0)
+    return measure
+
+
+def frame_measure(det, frame, reps: int = 5) -> Callable[[int, int, int], float]:
     """Timing function for single-frame detection (dog_detect) of `frame`."""
     import torch
     from . import dog
     blobs = dog.empty_blobs(det.cfg.blob_cap, frame.device)
     hist = torch.zeros(det.nbins_out, dtype=torch.int32, device=frame.device)
-
-    def measure(band: int, cps: int) -> float:
-        det.set_tiling(band, cps)
-        try:
-            return _time_ms(lambda: det.detect(frame, out=blobs, hist=hist), reps)
-        finally:
-            det.set_tiling(0, 1)
-    return measure
+    return _measure_with(det, lambda: det.detect(frame, out=blobs, hist=hist), reps)
 
 
-def batch_measure(det, table, reps: int = 3, **kw) -> Callable[[int, int], float]:
+def batch_measure(det, table, reps: int = 3, **kw) -> Callable[[int, int, int], float]:
     """Timing function for one batched launch over the frames of `table`."""
-
-    def measure(band: int, cps: int) -> float:
-        det.set_tiling(band, cps)
-        try:
-            return _time_ms(lambda: det.detect_batched(None, table=table, **kw), reps)
-        finally:
-            det.set_tiling(0, 1)
-    return measure
+    return _measure_with(det, lambda: det.detect_batched(None, table=table, **kw), reps)
 
 
 def tune_detector_frame(det, frame, n_sm: Optional[int] = None, cache_path: Optional[str] = None) -> TuneResult:
@@ -199,6 +206,7 @@ def tune_detector_frame(det, frame, n_sm: Optional[int] = None, cache_path: Opti
     n_sm = n_sm or torch.cuda.get_device_properties(frame.device).multi_processor_count
     t = Autotuner(n_sm, det.radii, cache_path)
     res = t.tune([tuple(frame.shape[-2:])], frame_measure(det, frame), mode="frame")
+    det.set_producer_warps(res.producer_warps)
     det.set_tiling(res.band, res.ctas_per_sm)
     return res
 
@@ -210,5 +218,6 @@ def tune_detector_batch(det, table, shapes, n_sm: Optional[int] = None, cache_pa
     n_sm = n_sm or torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     t = Autotuner(n_sm, det.radii, cache_path)
     res = t.tune(list(shapes), batch_measure(det, table, **kw), mode="batch")
+    det.set_producer_warps(res.producer_warps)
     det.set_tiling(res.band, res.ctas_per_sm)
     return res

@@ -219,40 +219,76 @@ static void free_all(dog_handle* h) {
 
 namespace dogk { void soft_free(dog_handle* h); }
 
-// Balance levels over the producer warps (every block, all of them wait for
-// the slowest at a barrier): first-fit decreasing at the smallest capacity
-// that packs all levels into the warps (raised one unit at a time from the
-// larger of the average load and the largest level).  Per level the cost is
-// two passes of tpad/8 tap blocks plus a fixed cost (set-up, pipeline fill and
+// Balance levels over the nw producer warps of a kernel form (every block,
+// all of them wait for the slowest at a barrier).  Per level the cost is two
+// passes of tpad/8 tap blocks plus a fixed cost (set-up, pipeline fill and
 // drain of both passes) of about 1.7 tap blocks of both passes (clock64 phase
-// timers).  On the 25-level ladder over 12 warps this gives a largest load of
-// 124 units where longest-processing-time-first gives 134.
-static void assign_levels(dog_handle* h) {
+// timers).  Over 12 warps: first-fit decreasing at the smallest capacity that
+// packs all levels (raised one unit at a time from the larger of the average
+// load and the largest level); on the 25-level ladder this gives a largest
+// load of 124 units where longest-processing-time-first gives 134, 2% faster
+// measured.  Over 8 warps: longest processing time first (each level, largest
+// first, to the least loaded warp), which spreads the levels over all warps
+// and measured up to 5% faster there than first-fit decreasing.
+static long long level_cost(const LevelInfo& L) { return 10 * (L.tpad / 8) + 17; }
+
+static void assign_levels(dog_handle* h, int nw) {
     const int K = h->K;
     std::vector<long long> cost(K);
     long long total = 0, biggest = 0;
     for (int i = 0; i < K; ++i) {
-        cost[i] = 10 * (h->base.lv[i].tpad / 8) + 17;
+        cost[i] = level_cost(h->base.lv[i]);
         total += cost[i];
         biggest = std::max(biggest, cost[i]);
     }
     std::vector<int> idx(K), owner(K);
     for (int i = 0; i < K; ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    for (long long cap = std::max(biggest, (total + NWARPS - 1) / NWARPS);; ++cap) {
+    if (nw == 8) {
         long long load[NWARPS] = {0};
-        bool fits = true;
         for (int i : idx) {
-            int w = 0;
-            while (w < NWARPS && load[w] + cost[i] > cap) ++w;
-            if (w == NWARPS) { fits = false; break; }
-            load[w] += cost[i];
-            owner[i] = w;
+            int best = 0;
+            for (int w = 1; w < nw; ++w)
+                if (load[w] < load[best]) best = w;
+            load[best] += cost[i];
+            owner[i] = best;
         }
-        if (fits) break;   // ends at the latest when cap reaches the total
+    } else {
+        for (long long cap = std::max(biggest, (total + nw - 1) / nw);; ++cap) {
+            long long load[NWARPS] = {0};
+            bool fits = true;
+            for (int i : idx) {
+                int w = 0;
+                while (w < nw && load[w] + cost[i] > cap) ++w;
+                if (w == nw) { fits = false; break; }
+                load[w] += cost[i];
+                owner[i] = w;
+            }
+            if (fits) break;   // ends at the latest when cap reaches the total
+        }
     }
+    h->base.nw = nw;
     for (int w = 0; w < NWARPS; ++w) h->base.warp_nlev[w] = 0;
     for (int i : idx) h->base.warp_lev[owner[i]][h->base.warp_nlev[owner[i]]++] = (unsigned char)i;
+}
+
+// Kernel form for a ladder when none is set: 12 producer warps for long
+// ladders whose largest level fits an even share of 12 warps (there the
+// extra warps hide latency), else 8 with more registers each (a few large
+// levels: their warps set the pace).  Measured on 96 frames of 1024 x 1024
+// (ms per launch, 12 / 8 warps): 25 levels sigma 0.8..7.9 (largest level 107
+// units of 1395) 10.82 / 11.72; 14 levels sigma 2..12.3 (147 of 1148)
+// 12.59 / 10.98; 12 levels sigma 1..11.6 (137 of 824) 9.95 / 9.33; 24 levels
+// sigma 2..2.8 (47 of 1128) 12.27 / 11.39, which this rule gets wrong (the
+// autotuner times both forms).
+static int default_producer_warps(const dog_handle* h) {
+    long long total = 0, biggest = 0;
+    for (int i = 0; i < h->K; ++i) {
+        const long long c = level_cost(h->base.lv[i]);
+        total += c;
+        biggest = std::max(biggest, c);
+    }
+    return (h->K >= 20 && 12 * biggest <= total) ? 12 : 8;
 }
 
 extern "C" {
@@ -413,7 +449,7 @@ int dog_create(const dog_config* cfg, dog_t** out) {
         off += b.lv[i].ring_rows * RING_STRIDE;
     }
     b.smem_bytes = off * (int)sizeof(float);
-    assign_levels(h);
+    assign_levels(h, default_producer_warps(h));
 
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -533,6 +569,14 @@ int dog_set_tiling(dog_t* h, int32_t band_rows, int32_t ctas_per_sm) {
     h->ctas_per_sm = ctas_per_sm;
     return DOG_OK;
 }
+
+int dog_set_producer_warps(dog_t* h, int32_t n) {
+    if (!h || !(n == 0 || n == 8 || n == 12)) return DOG_ERR_INVALID;
+    assign_levels(h, n == 0 ? default_producer_warps(h) : n);
+    return DOG_OK;
+}
+
+int dog_get_producer_warps(const dog_t* h) { return h ? h->base.nw : DOG_ERR_INVALID; }
 
 // The contrast stretch applies to 12-bit frames when the handle's stretch_sat
 // is set (frames of more than 2^31 pixels are not supported then).

@@ -12,23 +12,22 @@ namespace dogk {
 
 // ---- fused strip kernel geometry --------------------------------------------
 // A CTA owns a strip of TX output columns and walks down a band of rows in
-// blocks of MB rows.  NWARPS producer warps each own a fixed set of scale
-// levels and run the blur passes; NCONS consumer warps form the DoG and run
-// the maximum test one block behind.
+// blocks of MB rows.  Producer warps each own a fixed set of scale levels and
+// run the blur passes; NCONS consumer warps form the DoG and run the maximum
+// test one block behind.  The kernel comes in two forms: 12 producer warps at
+// 128 registers per thread, or 8 at 168 (both with the 4 consumer warps).
+// Which is faster depends on the ladder (the host picks one, the autotuner
+// times both); 10, 14 or 16 producer warps were slower than 12 on the
+// 25-level ladder (level balance, spills).
 constexpr int TX = 32;
 constexpr int MB = 8;
-// 12 producer + 4 consumer warps run at 128 registers per thread; measured
-// against 8 + 4 at 168 registers this is 6% faster on the 25-level ladder,
-// and 10, 14 or 16 producer warps are slower (level balance, spills)
-constexpr int NWARPS = 12;                      // producer (blur) warps
+constexpr int NWARPS = 12;                      // producer warps of the larger form (table sizes)
 constexpr int NCONS = 4;                        // consumer (DoG + test) warps, two rows each
-constexpr int NPROD_T = NWARPS * 32;
-constexpr int NTHREADS = (NWARPS + NCONS) * 32;
 constexpr int RING_STRIDE = 32;    // floats per ring row (bank swizzle on row parity)
 constexpr int DSLOTS = 2 * MB + 2; // DoG-buffer rows: two blocks + 2 rows of history
 constexpr int MAX_LEVELS = DOG_MAX_LEVELS;
 static_assert(MB % NCONS == 0, "each consumer warp tests whole rows of a block");
-static_assert(NTHREADS <= 1024, "one CTA");
+static_assert((NWARPS + NCONS) * 32 <= 1024, "one CTA");
 
 // Internal pixel type: 12-bit counts contrast stretched with per-frame limits
 // (the public types are DOG_DTYPE_F32 and DOG_DTYPE_U16).
@@ -118,6 +117,7 @@ struct FusedParams {
     int w_off, w_total;
     int dmin, dmax;
     int smem_bytes;
+    int nw;                // producer warps of the kernel form (8 or 12)
     int warp_nlev[NWARPS];
     unsigned char warp_lev[NWARPS][MAX_LEVELS];
     LevelInfo lv[MAX_LEVELS];

@@ -250,6 +250,14 @@ class Detector:
     def set_tiling(self, band_rows: int, ctas_per_sm: int = 1):
         check(self.lib.dog_set_tiling(self.h, band_rows, ctas_per_sm), "dog_set_tiling")
 
+    def set_producer_warps(self, n: int = 0):
+        """Kernel form: 8 or 12 producer warps, 0 for the handle's default."""
+        check(self.lib.dog_set_producer_warps(self.h, n), "dog_set_producer_warps")
+
+    @property
+    def producer_warps(self) -> int:
+        return int(self.lib.dog_get_producer_warps(self.h))
+
     def profile(self, enable: bool = True):
         check(self.lib.dog_profile_enable(self.h, int(enable)), "dog_profile_enable")
 

@@ -42,20 +42,22 @@ def test_candidates_rank_single_frame():
 def test_tuner_picks_fastest_and_caches(tmp_path):
     calls = []
 
-    def measure(band, cps):
-        calls.append((band, cps))
-        return {256: 1.0, 0: 3.0}.get(band, 2.0) if band != 232 else float("inf")
+    def measure(band, cps, nw):
+        calls.append((band, cps, nw))
+        base = {256: 1.0, 0: 3.0}.get(band, 2.0) if band != 232 else float("inf")
+        return base * (0.9 if nw == 8 else 1.0)
 
     path = str(tmp_path / "tune.json")
     t = autotune.Autotuner(152, RADII, path)
     r = t.tune([(1024, 1024)], measure)
-    assert (r.band, r.ctas_per_sm, r.ms) == (256, 1, 1.0)
+    assert (r.band, r.ctas_per_sm, r.ms, r.producer_warps) == (256, 1, 0.9, 8)
+    assert {c[2] for c in calls} == {8, 12}     # both kernel forms timed
     n = len(calls)
     assert t.tune([(1024, 1024)], measure).band == 256
     assert len(calls) == n                 # cached
     t2 = autotune.Autotuner(152, RADII, path)   # reloaded from disk
     r2 = t2.tune([(1024, 1024)], measure)
-    assert (r2.band, r2.ms) == (256, 1.0) and len(calls) == n
+    assert (r2.band, r2.ms, r2.producer_warps) == (256, 0.9, 8) and len(calls) == n
     # another shape mix is another key
     t.tune([(128, 128), (512, 512)], measure, mode="batch")
     assert len(calls) > n
@@ -64,4 +66,4 @@ def test_tuner_picks_fastest_and_caches(tmp_path):
 def test_tuner_all_failed():
     t = autotune.Autotuner(152, RADII)
     with pytest.raises(RuntimeError):
-        t.tune([(64, 64)], lambda b, c: float("nan"))
+        t.tune([(64, 64)], lambda b, c, w: float("nan"))

@@ -159,6 +159,36 @@ def test_row_bands_match_whole_frame():
     det.set_tiling(0)
 
 
+@pytest.mark.parametrize("ladder", ["plif", "grad"])
+def test_kernel_forms_agree_bit_for_bit(ladder):
+    """The 8- and 12-producer-warp forms compute every level with the same
+    operations: D, candidates and the pruned blobs are identical, single frame
+    and batched, whichever form the handle picked by default."""
+    cfg = (dog.plif_config if ladder == "plif" else dog.grad_config)(max_h=300, max_w=200)
+    img = synth.plif_frame(synth.PLIF_SEED_BASE + 11, 300, 200)
+    det = dog.Detector(cfg)
+    assert det.producer_warps == (12 if ladder == "plif" else 8)
+    t = dev(img)
+    out = {}
+    for nw in (8, 12):
+        det.set_producer_warps(nw)
+        assert det.producer_warps == nw
+        D = det.debug_dog(t).cpu().numpy()
+        cand = sorted(zip(*det.candidates(t).to_numpy()))
+        b, h, _ = det.detect(t)
+        bb, cc, hh = det.detect_batched([t, t[:150, :120].contiguous()])
+        torch.cuda.synchronize()
+        out[nw] = (D, cand, sorted(zip(*b.to_numpy())), h.cpu().numpy(), cc.cpu().numpy(), hh.cpu().numpy())
+    assert np.array_equal(out[8][0], out[12][0])
+    for a, b in zip(out[8][1:], out[12][1:]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+    det.set_producer_warps(0)
+    assert det.producer_warps == (12 if ladder == "plif" else 8)
+    with pytest.raises(_lib.DogError) as e:
+        det.set_producer_warps(10)
+    assert e.value.code == _lib.DOG_ERR_INVALID
+
+
 def test_capacity_overflow_reports_true_count():
     det = dog.Detector(dog.small_frame_config())
     img = dev(synth.small_blob_frame(1))
