@@ -129,11 +129,14 @@ def measured_peaks():
         return {}
 
 
+FUSED_SOURCES = ("dog_fused_forms.cuh", "dog_fused.cu", "dog_fused_w8.cu", "dog_device.cuh", "dog_internal.cuh")
+
+
 def fused_kernel_sha():
-    """sha256 over the fused kernel's sources (kernel file, device helpers,
-    shared parameter header), in that order."""
+    """sha256 over the fused kernel's sources (kernel forms, the two files that
+    instantiate them, device helpers, shared parameter header), in that order."""
     h = hashlib.sha256()
-    for f in ("dog_fused.cu", "dog_device.cuh", "dog_internal.cuh"):
+    for f in FUSED_SOURCES:
         with open(os.path.join(ROOT, "paper_2010_08486_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -368,7 +371,7 @@ def batched_leg(local, cache_path, reps=5):
             "dtype": "f32"}
 
 
-def diff_leg(local, reps=3):
+def diff_leg(local, cache_path=None, reps=3):
     """Differentiable form: 16 FP32 1024^2 frames through the soft blob-volume
     histogram with 12 learnable sigmas 1.25^k; forward + backward (gradients
     with respect to the frames and the sigmas), against the plain forward
@@ -380,7 +383,8 @@ def diff_leg(local, reps=3):
     frames = torch.from_numpy(np.stack(arrs)).cuda()
     det = dog.Detector(dog.grad_config())
     from paper_2010_08486_gb300 import autotune
-    tuned = autotune.tune_detector_frame(det, frames[0])   # row bands for 1024^2 frames, this ladder
+    # row bands and kernel form for 1024^2 frames, this ladder
+    tuned = autotune.tune_detector_frame(det, frames[0], cache_path=cache_path)
     sig0 = torch.tensor([1.25 ** k for k in range(12)], dtype=torch.float32, device="cuda")
     with torch.no_grad():
         tgt_frames = torch.from_numpy(np.stack(_pool_frames(
@@ -764,7 +768,7 @@ def run_ours(a):
                                       "for %.0f s (continuous batching)" % a.serve_seconds}
     if not a.no_forms:
         line["batched_uneven"] = batched_leg(local, a.tune_cache)
-        line["differentiable"] = diff_leg(local)
+        line["differentiable"] = diff_leg(local, a.tune_cache)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(counts_u16)
@@ -783,7 +787,7 @@ def run_leg(a):
     if a.leg == "batched":
         res = batched_leg(local, a.tune_cache)
     elif a.leg == "differentiable":
-        res = diff_leg(local)
+        res = diff_leg(local, a.tune_cache)
     elif a.leg == "spheres":
         res = spheres_leg(local)
     else:
