@@ -146,6 +146,32 @@ def test_u16_ingest_matches_f32():
     full_check(cfg, counts, det=det, img_t=t16)
 
 
+def test_u16_pitched_and_offset_frames_match_f32():
+    """A 12-bit frame given contiguously, with a pitch of 2 mod 4 counts and a
+    base offset by one count, or padded to a pitch of 324, single and
+    batched, gives the f32 path's D and candidates exactly."""
+    counts = synth.plif_frame_u16(synth.PLIF_SEED_BASE + 3, 256, 320)
+    cfg = dog.plif_config(max_h=256, max_w=320)
+    det = dog.Detector(cfg)
+    want_D = det.debug_dog(dev(synth.u16_to_f32(counts))).cpu().numpy()
+    want_c = sorted(zip(*det.candidates(dev(synth.u16_to_f32(counts))).to_numpy()))
+    wide = np.zeros((256, 326), np.uint16)
+    wide[:, 1:321] = counts
+    wide_t = dev(wide.view(np.int16))
+    views = {"contiguous": dev(counts.view(np.int16)),
+             "pitch_326": wide_t[:, 1:321],                 # pitch 2 mod 4, base 2 bytes off
+             "pitch_324": dev(np.pad(counts, ((0, 0), (0, 4))).view(np.int16))[:, :320]}
+    for name, t in views.items():
+        assert np.array_equal(det.debug_dog(t).cpu().numpy(), want_D), name
+        assert sorted(zip(*det.candidates(t).to_numpy())) == want_c, name
+    _, cnt, hist = det.detect_batched(list(views.values()))
+    b, h, _ = det.detect(views["contiguous"])
+    torch.cuda.synchronize()
+    assert cnt.cpu().tolist() == [b.n()] * 3
+    for f in range(3):
+        assert np.array_equal(hist[f].cpu().numpy(), h.cpu().numpy())
+
+
 def test_row_bands_match_whole_frame():
     img = synth.plif_frame(synth.PLIF_SEED_BASE + 7, 300, 200)
     det = dog.Detector(dog.plif_config(max_h=300, max_w=200))
