@@ -128,9 +128,10 @@ __global__ void fft_pad_kernel(const void* img, int dtype, int H, int W, int pit
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
     if (X >= W + 2 * R) return;
     const int lo = dtype == DTYPE_U16_STRETCH ? lohi[0] : 0, hi = dtype == DTYPE_U16_STRETCH ? lohi[1] : 0;
+    const float rcp = stretch_rcp(lo, hi);
     const int x = refl(X - R, W);
     for (int Y = blockIdx.y; Y < H + 2 * R; Y += gridDim.y)
-        pad[(size_t)Y * Wp + X] = raw_to_px(load_raw(img, dtype, pitch, refl(Y - R, H), x), dtype, lo, hi);
+        pad[(size_t)Y * Wp + X] = raw_to_px(load_raw(img, dtype, pitch, refl(Y - R, H), x), dtype, lo, hi, rcp);
 }
 
 // spectra of all levels: specs[i] = spec * gy[i][ky] * gx[i][kx]

@@ -119,6 +119,7 @@ struct TileCtx {
     const void* img;
     int dtype, H, W, pitch;
     int st_lo, st_hi;   // contrast-stretch limits (DTYPE_U16_STRETCH)
+    float st_rcp;       // stretch_rcp(st_lo, st_hi)
     int frame;
     int x0, y0, y1;
     dog_blob* blobs;
@@ -244,7 +245,7 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
 #pragma unroll
             for (int k = 0; k < NPF; ++k) {
                 const int cc = lane + 32 * k;
-                if (cc < ncols) dst[cc] = raw_to_px(pf[k], tc.dtype, tc.st_lo, tc.st_hi);
+                if (cc < ncols) dst[cc] = raw_to_px(pf[k], tc.dtype, tc.st_lo, tc.st_hi, tc.st_rcp);
             }
         }
         if (b >= 0) bar_arrive(BAR_FULL + (b & 1), NTHREADS);
@@ -562,7 +563,7 @@ __device__ __forceinline__ void process_tile(const FusedParams& p, float* sm, Sm
                 if (i < total) {
                     const int rr = i / ncols, cc = i - rr * ncols;
                     in[((y0 + rr - yorg) & (p.in_rows - 1)) * p.in_stride + cc] =
-                        raw_to_px(v[u], tc.dtype, tc.st_lo, tc.st_hi);
+                        raw_to_px(v[u], tc.dtype, tc.st_lo, tc.st_hi, tc.st_rcp);
                 }
             }
         }
@@ -624,6 +625,7 @@ __global__ void __launch_bounds__((NW + NCONS) * 32, 1) dog_fused_kernel(const _
         tc.img = p.img; tc.dtype = p.dtype; tc.H = p.H; tc.W = p.W; tc.pitch = p.pitch; tc.frame = 0;
         tc.st_lo = tc.dtype == DTYPE_U16_STRETCH ? p.lohi[0] : 0;
         tc.st_hi = tc.dtype == DTYPE_U16_STRETCH ? p.lohi[1] : 0;
+        tc.st_rcp = stretch_rcp(tc.st_lo, tc.st_hi);
         const int strip = blockIdx.x % p.n_strips;
         const int band = blockIdx.x / p.n_strips;
         tc.x0 = strip * TX;
@@ -652,6 +654,7 @@ __global__ void __launch_bounds__((NW + NCONS) * 32, 1) dog_fused_kernel(const _
             tc.img = f.img; tc.dtype = f.dtype; tc.H = f.h; tc.W = f.w; tc.pitch = f.pitch; tc.frame = lo;
             tc.st_lo = tc.dtype == DTYPE_U16_STRETCH ? p.lohi[2 * lo] : 0;
             tc.st_hi = tc.dtype == DTYPE_U16_STRETCH ? p.lohi[2 * lo + 1] : 0;
+            tc.st_rcp = stretch_rcp(tc.st_lo, tc.st_hi);
             tc.x0 = (local % f.n_strips) * TX;
             const int band = local / f.n_strips;
             const int bh = f.band;

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(RES_THREADS) dog_resolve_kernel(const __grid_c
         }
         const int st_lo = dtype == DTYPE_U16_STRETCH ? p.lohi[2 * e.frame] : 0;
         const int st_hi = dtype == DTYPE_U16_STRETCH ? p.lohi[2 * e.frame + 1] : 0;
+        const float st_rcp = stretch_rcp(st_lo, st_hi);
         const int lx = e.x % TX;
         const int xn = (lx == 0) ? e.x - 1 : e.x + 1;   // the column held by the other strip
         const int l = e.level;
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(RES_THREADS) dog_resolve_kernel(const __grid_c
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int jj = j + u * rpp;
-                        if (jj < ph) patch[jj * pw + cc] = raw_to_px(v[u], dtype, st_lo, st_hi);
+                        if (jj < ph) patch[jj * pw + cc] = raw_to_px(v[u], dtype, st_lo, st_hi, st_rcp);
                     }
                 }
             }

@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(LIM_THREADS) stretch_limits_kernel(const dog_f
 __global__ void __launch_bounds__(256) stretch_apply_kernel(const uint16_t* img, int H, int W, int pitch,
                                                             const int* lohi, float* out, int out_pitch) {
     const int lo = lohi[0], hi = lohi[1];
+    const float rcp = stretch_rcp(lo, hi);
     for (int y = blockIdx.y; y < H; y += gridDim.y) {
         const uint16_t* src = img + (size_t)y * pitch;
         float* dst = out + (size_t)y * out_pitch;
@@ -122,10 +123,10 @@ __global__ void __launch_bounds__(256) stretch_apply_kernel(const uint16_t* img,
             if (vec && x + 4 <= W) {
                 const uint2 v = __ldg(reinterpret_cast<const uint2*>(src + x));
                 *reinterpret_cast<float4*>(dst + x) =
-                    make_float4(stretch_px(v.x & 0xffffu, lo, hi), stretch_px(v.x >> 16, lo, hi),
-                                stretch_px(v.y & 0xffffu, lo, hi), stretch_px(v.y >> 16, lo, hi));
+                    make_float4(stretch_px(v.x & 0xffffu, lo, hi, rcp), stretch_px(v.x >> 16, lo, hi, rcp),
+                                stretch_px(v.y & 0xffffu, lo, hi, rcp), stretch_px(v.y >> 16, lo, hi, rcp));
             } else {
-                for (int u = x; u < x + 4 && u < W; ++u) dst[u] = stretch_px(__ldg(src + u), lo, hi);
+                for (int u = x; u < x + 4 && u < W; ++u) dst[u] = stretch_px(__ldg(src + u), lo, hi, rcp);
             }
         }
     }
