@@ -230,7 +230,12 @@ namespace dogk { void soft_free(dog_handle* h); }
 // measured.  Over 8 warps: longest processing time first (each level, largest
 // first, to the least loaded warp), which spreads the levels over all warps
 // and measured up to 5% faster there than first-fit decreasing.
-static long long level_cost(const LevelInfo& L) { return 10 * (L.tpad / 8) + 17; }
+// A level whose 2r + 1 taps are one past a multiple of 8 runs its last tap
+// alone (8 FMAs instead of a block of 64, no further loads): 8 units less.
+static long long level_cost(const LevelInfo& L) {
+    const bool tail = ((2 * L.r + 1) & 7) == 1;
+    return 10 * (L.tpad / 8) + 17 - (tail ? 8 : 0);
+}
 
 static void assign_levels(dog_handle* h, int nw) {
     const int K = h->K;

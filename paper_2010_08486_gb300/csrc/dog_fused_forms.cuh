@@ -50,11 +50,19 @@ __device__ __forceinline__ void fma_block(float (&acc)[8], const float (&A)[8], 
         for (int k = 0; k < 8; ++k) acc[k] = __fmaf_rn(w[u], (k + u < 8) ? A[k + u] : B[k + u - 8], acc[k]);
 }
 
+// The single last tap of a level whose 2r + 1 taps are one more than a
+// multiple of 8 (the rest of its padded block is zeros): out[k] += w * Y[k],
+// Y the window after the last full tap block.
+__device__ __forceinline__ void tap1(float (&acc)[8], const float (&Y)[8], float w) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = __fmaf_rn(w, Y[k], acc[k]);
+}
+
 // Horizontal: inputs are consecutive floats of one shared-memory row.
 // Output: 8 floats of one ring row, written as two float4 whose order is
 // swapped on odd rows (bank swizzle; `odd` is the ring row's parity).
 __device__ __forceinline__ void hpass(const float* __restrict__ src, float* __restrict__ dst, int odd,
-                                      const float4* __restrict__ w4, int nb) {
+                                      const float4* __restrict__ w4, int nb, bool tail) {
     float acc[8], A[8], B[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) { acc[k] = 0.0f; A[k] = src[k]; }
@@ -63,13 +71,19 @@ __device__ __forceinline__ void hpass(const float* __restrict__ src, float* __re
 #pragma unroll
         for (int k = 0; k < 8; ++k) B[k] = src[k];
         fma_block(acc, A, B, w4[0], w4[1]);
-        if (--nb == 0) break;
+        if (--nb == 0) {
+            if (tail) tap1(acc, B, w4[2].x);
+            break;
+        }
         src += 8;
         w4 += 2;
 #pragma unroll
         for (int k = 0; k < 8; ++k) A[k] = src[k];
         fma_block(acc, B, A, w4[0], w4[1]);
-        if (--nb == 0) break;
+        if (--nb == 0) {
+            if (tail) tap1(acc, A, w4[2].x);
+            break;
+        }
         src += 8;
         w4 += 2;
     }
@@ -84,7 +98,7 @@ __device__ __forceinline__ void hpass(const float* __restrict__ src, float* __re
 // read in blocks of 8 rows starting at ring row r0 (a multiple of 8); lane x
 // holds column x, stored at x on even rows and x ^ 4 on odd rows.
 __device__ __forceinline__ void vpass(const float* __restrict__ ring, int lane, int C, int r0,
-                                      const float4* __restrict__ w4, int nb, float (&acc)[8]) {
+                                      const float4* __restrict__ w4, int nb, bool tail, float (&acc)[8]) {
     const float* pe = ring + lane;
     const float* po = ring + (lane ^ 4);
     float A[8], B[8];
@@ -100,14 +114,20 @@ __device__ __forceinline__ void vpass(const float* __restrict__ ring, int lane, 
 #pragma unroll
         for (int k = 0; k < 8; ++k) B[k] = ((k & 1) ? po : pe)[(r + k) * RING_STRIDE];
         fma_block(acc, A, B, w4[0], w4[1]);
-        if (--nb == 0) break;
+        if (--nb == 0) {
+            if (tail) tap1(acc, B, w4[2].x);
+            break;
+        }
         r += 8;
         if (r == C) r = 0;
         w4 += 2;
 #pragma unroll
         for (int k = 0; k < 8; ++k) A[k] = ((k & 1) ? po : pe)[(r + k) * RING_STRIDE];
         fma_block(acc, B, A, w4[0], w4[1]);
-        if (--nb == 0) break;
+        if (--nb == 0) {
+            if (tail) tap1(acc, A, w4[2].x);
+            break;
+        }
         r += 8;
         if (r == C) r = 0;
         w4 += 2;
@@ -218,19 +238,21 @@ __device__ __forceinline__ void produce(const FusedParams& p, float* sm, SmemSma
             const int r0 = ss.rpos[i];     // 8b mod C; the chunk written now goes 8 rows before
             if (b + L.e >= 0) {
                 float* ring = sm + L.ring_off;
-                const int nb = L.tpad >> 3;
+                // 2r + 1 = 8 (nb - 1) + 1: nb - 1 full tap blocks and one last tap
+                const bool tail = ((2 * L.r + 1) & 7) == 1;
+                const int nb = (L.tpad >> 3) - (tail ? 1 : 0);
                 {
                     const int rho = lane >> 2, g = lane & 3;
                     const int yy = yb + L.delta + rho;     // input row of this lane
                     const float* src = in + ((yy - yorg) & (CIN - 1)) * S + (R - L.r) + 8 * g;
                     const int wrow = (r0 >= MB ? r0 - MB : r0 + C - MB) + rho;
                     hpass(src, ring + wrow * RING_STRIDE + 8 * g, rho & 1,
-                          reinterpret_cast<const float4*>(sm + p.w_off + L.hoff), nb);
+                          reinterpret_cast<const float4*>(sm + p.w_off + L.hoff), nb, tail);
                 }
                 __syncwarp();
                 if (b >= 0) {
                     float acc[8];
-                    vpass(ring, lane, C, r0, reinterpret_cast<const float4*>(sm + p.w_off + L.woff), nb, acc);
+                    vpass(ring, lane, C, r0, reinterpret_cast<const float4*>(sm + p.w_off + L.woff), nb, tail, acc);
                     float* dcol = dbuf + i * DSLOTS * TX + lane;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) dcol[dslot(s0 + k) * TX] = acc[k];
