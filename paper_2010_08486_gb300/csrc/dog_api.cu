@@ -638,20 +638,9 @@ static ResolveParams resolve_params(const dog_handle* h, const FusedParams& f) {
         r.woff[i] = h->woff[i];
         r.r[i] = h->rad[i];
     }
-    r.mode = f.mode;
     r.blobs = f.blobs;
     r.cap = f.cap;
     r.count = f.count;
-    r.kappa = f.kappa;
-    r.dkappa = f.dkappa;
-    r.gH = f.gH;
-    r.nbins = f.nbins;
-    r.thr = f.thr;
-    r.inv_T = f.inv_T;
-    r.soft_out = f.soft_out;
-    r.A = f.A;
-    r.dc_acc = f.dc_acc;
-    r.dt_acc = f.dt_acc;
     r.status = h->d_status;
     return r;
 }

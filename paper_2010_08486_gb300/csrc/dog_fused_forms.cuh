@@ -24,8 +24,11 @@
 // any response bit for bit.  Then all threads form D in place and test the
 // previous block's rows against their 26 neighbours; survivors are compacted
 // with one warp ballot and one atomic per warp.  Neighbours in the adjacent
-// strip are not held here: a candidate at a strip edge is queued and the
-// resolve kernel recomputes the few responses it needs.
+// strip are not held here: in detection a candidate at a strip edge is
+// queued and the resolve kernel recomputes the few responses it needs; the
+// soft modes, which keep every local maximum (thousands at strip edges per
+// frame), instead step 32-column strips by 30 so that lanes 0 and 31 are
+// only neighbours and every voxel a strip owns has its whole neighbourhood.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -383,12 +386,13 @@ __device__ __forceinline__ float d_at(const float* colp, const float* cs, int l,
 // horizontal maximum through two warp shuffles -> m_l; a voxel is a
 // candidate iff D_l(y, x) >= max(m_{l-1}, m_l, m_{l+1}) (it equals its 3x3x3
 // maximum).  Neighbours outside the frame count as -inf; those in the
-// adjacent strip are left to the resolve kernel (the candidate is queued).
+// adjacent strip are left to the resolve kernel (the candidate is queued),
+// unless the strips overlap (soft modes).
 // The plane loop is unrolled over PB >= P planes without branches (planes
 // l >= P read plane P and are masked to -inf), keeping m and D in registers;
 // candidates are collected in a per-lane bit mask and compacted afterwards
 // (they are rare).
-template <int NW, int PB, bool FULL>
+template <int NW, bool BATCHED, int PB, bool FULL>
 __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc, int nblk) {
     constexpr int NTHREADS = (NW + NCONS) * 32;
     const int cw = (threadIdx.x >> 5) - NW;   // 0 .. NCONS-1
@@ -401,8 +405,13 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
     const float thr = soft ? -INFINITY : p.thr;   // D > thr is not applied to soft maxima
     const int x = lane;
     const int gx = tc.x0 + x;
-    const bool col_ok = gx < tc.W;
-    const bool edge_x = (x == 0 && tc.x0 > 0) || (x == TX - 1 && gx + 1 < tc.W);
+    const bool col_ok = gx >= 0 && gx < tc.W;   // a real column (neighbours of owned voxels)
+    // voxels this lane settles: with overlapping strips lanes 0 and TX-1 are
+    // only neighbours (the adjacent strips own those columns); otherwise a
+    // strip-edge voxel whose neighbours lie in the adjacent strip is queued
+    const bool overlap = !BATCHED && p.overlap;   // (single-frame launches only)
+    const bool own = col_ok && (!overlap || (x >= 1 && x <= TX - 2));
+    const bool edge_x = !overlap && ((x == 0 && tc.x0 > 0) || (x == TX - 1 && gx + 1 < tc.W));
     const float* colp = dbuf + x;
 
     for (int b = 0; b < nblk; ++b) {
@@ -416,7 +425,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
             const int s0 = (MB * b + wa) % DSLOTS, s1 = (MB * b + wa + 1) % DSLOTS;
             const int s2 = (MB * b + wa + 2) % DSLOTS, s3 = (MB * b + wa + 3) % DSLOTS;
             const bool a_up = ya - 1 >= 0, a_dn = ya + 1 < tc.H, b_up = ya >= 0, b_dn = ya + 2 < tc.H;
-            if (a_up && b_dn && tc.x0 + TX <= tc.W)
+            if (a_up && b_dn && tc.x0 >= 0 && tc.x0 + TX <= tc.W)
                 test_planes2<PB, FULL, false>(colp, ss.c, P, s0, s1, s2, s3, a_up, a_dn, b_up, b_dn, col_ok, thr,
                                               cm2a, cm2b);
             else
@@ -433,7 +442,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
             const int sp1 = (MB * b + w + 2) % DSLOTS;   // row y+1
             const bool ym_ok = y - 1 >= 0, yp_ok = y + 1 < tc.H;
             if (mode == MODE_DUMP) {
-                if (row_ok && col_ok) {
+                if (row_ok && own) {
                     for (int l = 0; l < P; ++l) {
                         const float* pl = colp + l * DSLOTS * TX;
                         p.dump[((size_t)l * tc.H + y) * tc.W + gx] =
@@ -449,7 +458,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                 cmask = test_planes<PB, FULL, false>(colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok, thr);
             else
                 cmask = test_planes<PB, FULL, true>(colp, ss.c, P, sm1, sc, sp1, ym_ok, yp_ok, col_ok, thr);
-            if (!(row_ok && col_ok)) cmask = 0u;
+            if (!(row_ok && own)) cmask = 0u;
             const unsigned dmask = edge_x ? 0u : cmask;   // settled here
             const unsigned pmask = edge_x ? cmask : 0u;   // queued for the resolve kernel
             // ---- queued strip-edge candidates (lanes 0 and 31 only)
@@ -537,7 +546,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
                             atomicAdd(&ss.dc[l], G * d / ss.c[l]);
                             atomicAdd(&ss.dt[l], s * ss.gdk[l]);
                         }
-                        if (row_ok && col_ok) {
+                        if (row_ok && own) {
                             p.A[((size_t)l * tc.H + y) * tc.W + gx] = ss.c[l] * G - (l > 0 ? ss.c[l - 1] * Gprev : 0.0f);
                             if (l == P - 1) p.A[((size_t)(l + 1) * tc.H + y) * tc.W + gx] = -ss.c[l] * G;
                         }
@@ -551,7 +560,7 @@ __device__ __forceinline__ void consume(const FusedParams& p, float* sm, SmemSma
     }
 }
 
-template <int NW, int PB, bool FULL>
+template <int NW, bool BATCHED, int PB, bool FULL>
 __device__ __forceinline__ void process_tile(const FusedParams& p, float* sm, SmemSmall& ss, const TileCtx& tc) {
     constexpr int NTHREADS = (NW + NCONS) * 32, NPROD_T = NW * 32;
     const int tid = threadIdx.x;
@@ -596,7 +605,7 @@ __device__ __forceinline__ void process_tile(const FusedParams& p, float* sm, Sm
     }
     __syncthreads();
     if (tid < NPROD_T) produce<NW>(p, sm, ss, tc, emax, nblk);
-    else consume<NW, PB, FULL>(p, sm, ss, tc, nblk);
+    else consume<NW, BATCHED, PB, FULL>(p, sm, ss, tc, nblk);
     __syncthreads();
 }
 
@@ -650,12 +659,12 @@ __global__ void __launch_bounds__((NW + NCONS) * 32, 1) dog_fused_kernel(const _
         tc.st_rcp = stretch_rcp(tc.st_lo, tc.st_hi);
         const int strip = blockIdx.x % p.n_strips;
         const int band = blockIdx.x / p.n_strips;
-        tc.x0 = strip * TX;
+        tc.x0 = p.overlap ? strip * (TX - 2) - 1 : strip * TX;
         tc.y0 = band * p.band;
         tc.y1 = min(p.H, tc.y0 + p.band);
         tc.blobs = p.blobs;
         tc.count = p.count;
-        process_tile<NW, PB, FULL>(p, sm, ss, tc);
+        process_tile<NW, BATCHED, PB, FULL>(p, sm, ss, tc);
     } else {
         for (int q = tid; q < p.P; q += NTHREADS) ss.sig[q] = p.c[p.P + q];
         const long long n_tiles = p.ntiles_dev ? *p.ntiles_dev : p.n_tiles;
@@ -684,7 +693,7 @@ __global__ void __launch_bounds__((NW + NCONS) * 32, 1) dog_fused_kernel(const _
             tc.y1 = min(f.h, tc.y0 + bh);
             tc.blobs = p.blobs + f.blob_off;
             tc.count = p.count + lo;
-            process_tile<NW, PB, FULL>(p, sm, ss, tc);
+            process_tile<NW, BATCHED, PB, FULL>(p, sm, ss, tc);
         }
         if (tid == 0) {
             __threadfence();

@@ -76,6 +76,8 @@ struct FusedParams {
     const int* lohi;       // contrast-stretch limits (lo, hi) per frame (DTYPE_U16_STRETCH frames)
     int band;              // output rows per CTA (multiple of MB)
     int n_strips, n_bands;
+    int overlap;           // single frame: strips of TX columns step by TX - 2 from column -1, and
+                           // only lanes 1 .. TX-2 own their voxels (no strip-edge queue)
     // batched mode
     const FrameDesc* frames;
     int n_frames;
@@ -136,23 +138,9 @@ struct ResolveParams {
     const float* c;
     int woff[MAX_LEVELS];
     int r[MAX_LEVELS];
-    int mode;
     dog_blob* blobs;
     int cap;
     int* count;
-    // soft / backward
-    const float* kappa;
-    const float* dkappa;
-    const float* gH;
-    int nbins;
-    float thr, inv_T;
-    float* soft_out;
-    float* A;
-    double* dc_acc;
-    double* dt_acc;
-    dog_soft_max* rec;
-    int rec_cap;
-    int* rec_count;
     int* status;
 };
 

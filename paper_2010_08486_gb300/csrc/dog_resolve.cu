@@ -26,7 +26,8 @@ __host__ __device__ inline int resolve_smem_floats(int R) {
     return (2 * R + 3) * (2 * R + 1) + 4 * (2 * R + 3) + 4 * (2 * R + 1) + 16;
 }
 
-__global__ void __launch_bounds__(RES_THREADS) dog_resolve_kernel(const __grid_constant__ ResolveParams p) {
+// Eight CTAs per SM (the launch's grid cap): 32 registers per thread.
+__global__ void __launch_bounds__(RES_THREADS, 8) dog_resolve_kernel(const __grid_constant__ ResolveParams p) {
     extern __shared__ float rsm[];
     const int tid = threadIdx.x;
     const int npend = min(*p.pend_count, p.pend_cap);
@@ -131,48 +132,13 @@ __global__ void __launch_bounds__(RES_THREADS) dog_resolve_kernel(const __grid_c
                 }
             }
             if (keep) {
-                if (p.mode == MODE_CANDIDATES) {
-                    const int idx = atomicAdd(count, 1);
-                    if (idx < p.cap) {
-                        dog_blob bl;
-                        bl.x = e.x; bl.y = e.y; bl.level = l; bl.sigma = __ldg(p.c + p.P + l); bl.response = e.response;
-                        blobs[idx] = bl;
-                    } else {
-                        atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
-                    }
+                const int idx = atomicAdd(count, 1);
+                if (idx < p.cap) {
+                    dog_blob bl;
+                    bl.x = e.x; bl.y = e.y; bl.level = l; bl.sigma = __ldg(p.c + p.P + l); bl.response = e.response;
+                    blobs[idx] = bl;
                 } else {
-                    const float s = 1.0f / (1.0f + __expf(-(e.response - p.thr) * p.inv_T));
-                    if (p.mode == MODE_SOFT) {
-                        for (int b = 0; b < p.nbins; ++b) {
-                            const float k = p.kappa[l * p.nbins + b];
-                            if (k != 0.0f) atomicAdd(&p.soft_out[b], s * k);
-                        }
-                        if (p.rec != nullptr) {
-                            const int idx = atomicAdd(p.rec_count, 1);
-                            if (idx < p.rec_cap) {
-                                const float q = s * (1.0f - s) * p.inv_T;
-                                dog_soft_max m;
-                                m.x = e.x; m.y = e.y; m.level = l; m.q = q;
-                                m.qe = q * (e.response / __ldg(p.c + l));
-                                m.s = s;
-                                p.rec[idx] = m;
-                            } else {
-                                atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
-                            }
-                        }
-                    } else {
-                        float gk = 0.0f, gdk = 0.0f;
-                        for (int b = 0; b < p.nbins; ++b) {
-                            gk += p.gH[b] * p.kappa[l * p.nbins + b];
-                            gdk += p.gH[b] * p.dkappa[l * p.nbins + b];
-                        }
-                        const float cl = __ldg(p.c + l);
-                        const float G = gk * s * (1.0f - s) * p.inv_T;
-                        atomicAdd(&p.A[((size_t)l * H + e.y) * W + e.x], cl * G);
-                        atomicAdd(&p.A[((size_t)(l + 1) * H + e.y) * W + e.x], -cl * G);
-                        atomicAdd(&p.dc_acc[l], (double)(G * e.response / cl));
-                        atomicAdd(&p.dt_acc[l], (double)(s * gdk));
-                    }
+                    atomicCAS(p.status, 0, (int)DOG_ERR_CAPACITY);
                 }
             }
         }

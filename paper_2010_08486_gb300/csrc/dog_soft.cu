@@ -219,7 +219,11 @@ static FusedParams soft_fused(dog_handle* h, SoftWS* ws, const float* img, int H
     p.pitch = pitch;
     const int band = handle_band(h);
     p.band = (band > 0 && band < H) ? band : ((H + MB - 1) / MB) * MB;
-    p.n_strips = (W + TX - 1) / TX;
+    // overlapping strips (32 columns stepping by 30): every local maximum is
+    // settled inside the fused kernel, so no strip-edge resolve follows (the
+    // soft modes keep every maximum, thousands per frame at strip edges)
+    p.overlap = 1;
+    p.n_strips = (W + TX - 2 - 1) / (TX - 2);
     p.n_bands = (H + p.band - 1) / p.band;
     p.frames = nullptr;
     p.mode = mode;
@@ -234,43 +238,6 @@ static FusedParams soft_fused(dog_handle* h, SoftWS* ws, const float* img, int H
     p.inv_T = (float)(1.0 / handle_cfg(h).soft_T);
     p.status = handle_status(h);
     return p;
-}
-
-static ResolveParams soft_resolve(dog_handle* h, const FusedParams& f) {
-    ResolveParams r{};
-    r.pend = f.pend;
-    r.pend_count = f.pend_count;
-    r.pend_cap = f.pend_cap;
-    r.img = f.img;
-    r.dtype = f.dtype;
-    r.H = f.H;
-    r.W = f.W;
-    r.pitch = f.pitch;
-    r.K = f.K;
-    r.P = f.P;
-    r.w = f.w;
-    r.c = f.c;
-    for (int i = 0; i < f.K; ++i) {
-        r.woff[i] = f.lv[i].woff;
-        r.r[i] = f.lv[i].r;
-    }
-    r.mode = f.mode;
-    r.kappa = f.kappa;
-    r.dkappa = f.dkappa;
-    r.gH = f.gH;
-    r.nbins = f.nbins;
-    r.thr = f.thr;
-    r.inv_T = f.inv_T;
-    r.soft_out = f.soft_out;
-    r.A = f.A;
-    r.dc_acc = f.dc_acc;
-    r.dt_acc = f.dt_acc;
-    r.rec = f.rec;
-    r.rec_cap = f.rec_cap;
-    r.rec_count = f.rec_count;
-    r.status = handle_status(h);
-    (void)h;
-    return r;
 }
 
 #define SOFT_CUDA(x)                                                                  \
@@ -297,7 +264,6 @@ int soft_forward(dog_handle* h, const float* img, int H, int W, int pitch, const
         p.rec_count = rec_count;
     }
     SOFT_CUDA(timed_fused(h, p, p.n_strips * p.n_bands, s));
-    SOFT_CUDA(launch_resolve(soft_resolve(h, p), std::min(ws->pend_cap, 152 * 64), s));
     return DOG_OK;
 }
 
@@ -989,7 +955,6 @@ int soft_backward(dog_handle* h, const float* img, int H, int W, int pitch, cons
     p.dc_acc = ws->acc;
     p.dt_acc = ws->acc + P;
     SOFT_CUDA(timed_fused(h, p, p.n_strips * p.n_bands, s));
-    SOFT_CUDA(launch_resolve(soft_resolve(h, p), std::min(ws->pend_cap, 152 * 64), s));
     return adjoint_tail(h, ws, q, img, H, W, pitch, sig, gimg, gsig, true, s);
 }
 
