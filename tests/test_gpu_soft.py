@@ -114,6 +114,26 @@ def test_backward_matches_oracle_gradient(n, use_rec):
     assert np.linalg.norm(gs - osg) <= 1e-4 * np.linalg.norm(osg)
 
 
+@pytest.mark.parametrize("shape", [(40, 1), (40, 7), (33, 30), (37, 31), (50, 61)])
+def test_soft_narrow_frames_match_oracle(shape):
+    """The soft modes run 32-column strips stepping by 30 from column -1:
+    frames of one strip, of exactly 30 columns, of one column more, and of
+    two strips give the oracle's soft histogram and record every maximum the
+    oracle finds (decidable voxels), each once."""
+    h, w = shape
+    img = synth.plif_frame(synth.GRAD_SEED_BASE + 7)[500:500 + h, 600:600 + w].copy()
+    cfg, det, p, sig0, sig = setup(img)
+    t = torch.from_numpy(img).cuda()
+    s = torch.from_numpy(sig).cuda()
+    rad = np.asarray(det.radii)
+    rec = dog.SoftMaxima(1 << 16, "cuda")
+    H = det.soft_hist(t, s, rec=rec).cpu().numpy().astype(np.float64)
+    assert det.status() == 0
+    mask = check_record_mask(rec, img, sig, rad, p)
+    Ho = oracle.soft_hist(img.astype(np.float64), sig.astype(np.float64), rad, p, sig0, mask)
+    assert np.abs(H - Ho).max() <= 1e-4 * Ho.sum() + 1e-5
+
+
 @pytest.mark.parametrize("use_rec", [False, True])
 def test_backward_odd_shape_matches_oracle(use_rec):
     # width not a multiple of 4 (no vectorised staging), height not a multiple
